@@ -1,0 +1,133 @@
+/*
+ * dil.h -- C ABI of the batched CRYSTALS-Dilithium (round 3) engine for one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Operations follow arXiv 2211.12265 ("High-Throughput GPU Implementation of
+ * Dilithium Post-Quantum Digital Signature"):
+ *   Gen    -- Alg 1 (section 2.3), keys from a 32-byte seed zeta;
+ *   Sign   -- Alg 2, deterministic (rho' = H(K || mu)), rejection loop;
+ *   Verify -- Alg 3;
+ * over batches of independent tasks (section 3.1 task-level batching), with
+ * the parameters of Table 1 for levels 2, 3 and 5.  Byte layouts of keys and
+ * signatures are the round-3 little-endian encodings:
+ *   pk  = rho (32) || t1 (k x 320)                         1312 / 1952 / 2592 B
+ *   sk  = rho || K || tr (3 x 32) || s1 || s2 || t0        2528 / 4000 / 4864 B
+ *   sig = c~ (32) || z (l x 576|640) || h (omega + k)      2420 / 3293 / 4595 B
+ *
+ * Conventions for every entry point unless stated otherwise:
+ *   - Data pointers are DEVICE pointers owned by the caller; batched arrays are
+ *     task-major and densely packed (task i's pk starts at pk + i * PK).
+ *     Messages are one concatenated byte array `msg` with n + 1 byte offsets
+ *     `msg_off` (task i's message is msg[msg_off[i] .. msg_off[i+1]) and may be
+ *     empty; msg may be NULL when every message is empty).  No alignment is
+ *     required.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     asynchronous on that stream: the return value reports argument and
+ *     launch errors only; per-task results are written to device memory.
+ *   - The context owns a device workspace (the scratch the kernels need); the
+ *     caller owns everything else.  Calls that share one context must not run
+ *     concurrently on the GPU (use one context per concurrently used stream).
+ *   - Return values are dil_status codes (0 = success).
+ */
+#ifndef DIL_H
+#define DIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DIL_OK = 0,
+    DIL_EINVAL = -1,   /* bad level, NULL pointer, size out of range */
+    DIL_ENOMEM = -2,   /* workspace does not fit the budget or the device */
+    DIL_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    DIL_ETIMEOUT = -4, /* a bounded device-side wait ran out (persistent kernels) */
+    DIL_EITER = -5     /* per task: the Sign loop hit its repetition cap */
+} dil_status;
+
+typedef struct dil_ctx dil_ctx;
+
+/* Sizes in bytes of pk, sk and signature for level 2, 3 or 5 (Table 1 widths).
+ * Any output pointer may be NULL.  Returns DIL_EINVAL for another level. */
+int dil_sizes(int level, size_t *pk_bytes, size_t *sk_bytes, size_t *sig_bytes);
+
+/* Human-readable name of a status code (static string). */
+const char *dil_status_string(int status);
+
+/* Creates a context bound to CUDA device `device`.  workspace_budget caps the
+ * device scratch the context may allocate (0 = 8 GiB).  Batches that need more
+ * scratch than the budget are processed in several launches on the stream. */
+int dil_ctx_create(int device, size_t workspace_budget, dil_ctx **out);
+/* Frees the workspace after synchronising the device.  NULL is accepted. */
+int dil_ctx_destroy(dil_ctx *ctx);
+
+/* Caps the number of Sign loop repetitions (Alg 2 l.5-19) for this context.
+ * 0 restores the default cap implied by the 16-bit nonce (kappa + l - 1 <= 65535).
+ * Tasks that reach the cap get DIL_EITER and an all-zero signature. */
+int dil_set_max_iter(dil_ctx *ctx, int max_iter);
+
+/* Alg 1 (Gen): n 32-byte seeds -> n public keys and n secret keys. */
+int dil_keygen(dil_ctx *ctx, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
+               void *stream);
+
+/* Alg 2 (Sign, deterministic): n secret keys and messages -> n signatures.
+ * task_status (nullable, n int32): DIL_OK or DIL_EITER per task. */
+int dil_sign(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+             const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream);
+
+/* As dil_sign, also writing the number of loop repetitions per task
+ * (iterations: nullable, n int32). */
+int dil_sign_ex(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+                const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, int32_t *iterations,
+                void *stream);
+
+/* Alg 3 (Verify): ok[i] = 1 when signature i is valid for message i under
+ * public key i, else 0.  A malformed signature is a reject, not an error. */
+int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
+               const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream);
+
+/* Host-buffer forms of the three operations (all pointers are HOST pointers;
+ * msg_off too).  They copy inputs to the device, run on `stream`, copy the
+ * results back and synchronise the stream before returning. */
+int dil_keygen_host(dil_ctx *ctx, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
+                    void *stream);
+int dil_sign_host(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+                  const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream);
+int dil_verify_host(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
+                    const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream);
+
+/* ----------------------------------------------------------------------------
+ * Test-only entry points: single primitives of the hot path, for component
+ * parity against the oracle.  Same conventions (device pointers, async).
+ * ------------------------------------------------------------------------- */
+
+/* SHAKE128 (rate 168, kind = 128) or SHAKE256 (rate 136, kind = 256) of n byte
+ * strings (in, in_off as for messages) -> outlen bytes each (out: n x outlen). */
+int dil_test_shake(dil_ctx *ctx, int kind, size_t n, const uint8_t *in, const uint64_t *in_off,
+                   uint8_t *out, size_t outlen, void *stream);
+/* Forward (inverse = 0) or inverse (inverse = 1) NTT of n polynomials of 256
+ * int32 coefficients (any representatives with |a| < q); outputs in [0, q). */
+int dil_test_ntt(dil_ctx *ctx, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream);
+/* ExpandA of n seeds rho (n x 32 bytes) -> n x k x l x 256 int32 in [0, q). */
+int dil_test_expand_a(dil_ctx *ctx, int level, size_t n, const uint8_t *rho, int32_t *ahat, void *stream);
+/* ExpandS of n seeds rho' (n x 64 bytes) -> n x (l + k) x 256 int32 (s1 then s2). */
+int dil_test_expand_s(dil_ctx *ctx, int level, size_t n, const uint8_t *rhop, int32_t *s, void *stream);
+/* ExpandMask of n (rho', kappa) pairs -> n x l x 256 int32. */
+int dil_test_expand_mask(dil_ctx *ctx, int level, size_t n, const uint8_t *rhop, const int32_t *kappa,
+                         int32_t *y, void *stream);
+/* SampleInBall of n seeds c~ (n x 32 bytes) -> n x 256 int32 in {-1, 0, 1}. */
+int dil_test_sample_in_ball(dil_ctx *ctx, int level, size_t n, const uint8_t *ctilde, int32_t *c,
+                            void *stream);
+/* Coefficient functions of section 2.3 on n values r in [0, q) (and z, h):
+ * out is n x 6 int32: Power2Round (r1, r0), Decompose (r1, r0),
+ * MakeHint(z, r), UseHint(h, r). */
+int dil_test_rounding(dil_ctx *ctx, int level, size_t n, const int32_t *r, const int32_t *z,
+                      const uint8_t *h, int32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIL_H */

@@ -1,0 +1,392 @@
+// C ABI of the batched Dilithium engine (declarations and contracts in
+// include/dil.h).  Host-side argument checking, the device workspace owned by a
+// context, batch chunking to the workspace budget, and the host-buffer forms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/dil.h"
+#include "dil_launch.h"
+
+struct dil_ctx {
+    int device = 0;
+    size_t budget = 0;
+    void *ws = nullptr;       // device scratch
+    size_t ws_bytes = 0;
+    int max_iter = 0;         // 0 = nonce cap
+    int warps[3] = {4, 4, 4}; // warps (tasks) per CTA for keygen / sign / verify
+    // host-form staging (device memory)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+constexpr size_t POLY_BYTES = 256 * sizeof(int32_t);
+
+bool level_ok(int level) { return level == 2 || level == 3 || level == 5; }
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DIL_ENOMEM : DIL_ECUDA; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Ensures at least `bytes` of workspace; returns DIL_OK or an error.
+int ensure_ws(dil_ctx *c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return DIL_OK;
+    if (bytes > c->budget) return DIL_ENOMEM;
+    if (c->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->ws = nullptr;
+        return DIL_ENOMEM;
+    }
+    c->ws_bytes = bytes;
+    return DIL_OK;
+}
+
+// Largest number of tasks per launch whose scratch fits the budget.
+size_t chunk_tasks(dil_ctx *c, int op, int level, size_t n) {
+    size_t per = dil::scratch_polys(op, level) * POLY_BYTES;
+    if (per == 0) return n;
+    size_t fit = c->budget / per;
+    size_t lim = std::min<size_t>(n, std::min<size_t>(fit, (size_t)1 << 30));
+    return lim;
+}
+
+void sizes_of(int level, size_t &pk, size_t &sk, size_t &sig) { dil_sizes(level, &pk, &sk, &sig); }
+
+}  // namespace
+
+extern "C" {
+
+int dil_sizes(int level, size_t *pk_bytes, size_t *sk_bytes, size_t *sig_bytes) {
+    size_t pk, sk, sig;
+    switch (level) {
+        case 2: pk = 1312; sk = 2528; sig = 2420; break;
+        case 3: pk = 1952; sk = 4000; sig = 3293; break;
+        case 5: pk = 2592; sk = 4864; sig = 4595; break;
+        default: return DIL_EINVAL;
+    }
+    if (pk_bytes) *pk_bytes = pk;
+    if (sk_bytes) *sk_bytes = sk;
+    if (sig_bytes) *sig_bytes = sig;
+    return DIL_OK;
+}
+
+const char *dil_status_string(int status) {
+    switch (status) {
+        case DIL_OK: return "ok";
+        case DIL_EINVAL: return "invalid argument";
+        case DIL_ENOMEM: return "out of workspace or device memory";
+        case DIL_ECUDA: return "CUDA error";
+        case DIL_ETIMEOUT: return "device wait timed out";
+        case DIL_EITER: return "sign repetition cap reached";
+    }
+    return "unknown status";
+}
+
+int dil_ctx_create(int device, size_t workspace_budget, dil_ctx **out) {
+    if (!out) return DIL_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return DIL_ECUDA;
+    }
+    if (device < 0 || device >= count) return DIL_EINVAL;
+    dil_ctx *c = new dil_ctx;
+    c->device = device;
+    c->budget = workspace_budget ? workspace_budget : ((size_t)8 << 30);
+    *out = c;
+    return DIL_OK;
+}
+
+int dil_ctx_destroy(dil_ctx *c) {
+    if (!c) return DIL_OK;
+    {
+        DeviceGuard g(c->device);
+        cudaDeviceSynchronize();
+        if (c->ws) cudaFree(c->ws);
+        if (c->stage) cudaFree(c->stage);
+    }
+    delete c;
+    return DIL_OK;
+}
+
+int dil_set_max_iter(dil_ctx *c, int max_iter) {
+    if (!c || max_iter < 0) return DIL_EINVAL;
+    c->max_iter = max_iter;
+    return DIL_OK;
+}
+
+int dil_keygen(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk, void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!seeds || !pk || !sk || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    size_t chunk = chunk_tasks(c, dil::OP_KEYGEN, level, n);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * dil::scratch_polys(dil::OP_KEYGEN, level) * POLY_BYTES);
+    if (rc) return rc;
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_keygen(level, m, seeds + 32 * s0, pk + pkb * s0, sk + skb * s0,
+                                           (int32_t *)c->ws, c->warps[0], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
+int dil_sign_ex(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
+                uint8_t *sig, int32_t *task_status, int32_t *iterations, void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!sk || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    int l = level == 2 ? 4 : level == 3 ? 5 : 7;
+    int cap = (65536 - l) / l + 1;
+    int max_iter = (c->max_iter > 0 && c->max_iter < cap) ? c->max_iter : cap;
+    size_t chunk = chunk_tasks(c, dil::OP_SIGN, level, n);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * dil::scratch_polys(dil::OP_SIGN, level) * POLY_BYTES);
+    if (rc) return rc;
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_sign(level, m, sk + skb * s0, msg, msg_off + s0, sig + sigb * s0,
+                                         task_status ? task_status + s0 : nullptr,
+                                         iterations ? iterations + s0 : nullptr, (int32_t *)c->ws, max_iter,
+                                         c->warps[1], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
+int dil_sign(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
+             uint8_t *sig, int32_t *task_status, void *stream) {
+    return dil_sign_ex(c, level, n, sk, msg, msg_off, sig, task_status, nullptr, stream);
+}
+
+int dil_verify(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg, const uint64_t *msg_off,
+               const uint8_t *sig, uint8_t *ok, void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!pk || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    size_t chunk = chunk_tasks(c, dil::OP_VERIFY, level, n);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * dil::scratch_polys(dil::OP_VERIFY, level) * POLY_BYTES);
+    if (rc) return rc;
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_verify(level, m, pk + pkb * s0, msg, msg_off + s0, sig + sigb * s0, ok + s0,
+                                           (int32_t *)c->ws, c->warps[2], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
+// ---------------------------------------------------------------- host forms
+namespace {
+
+// Device staging for the host forms: grows on demand (not part of the budget).
+int ensure_stage(dil_ctx *c, size_t bytes) {
+    if (bytes <= c->stage_bytes) return DIL_OK;
+    if (c->stage) {
+        cudaDeviceSynchronize();
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    if (cudaMalloc(&c->stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DIL_ENOMEM;
+    }
+    c->stage_bytes = bytes;
+    return DIL_OK;
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int dil_keygen_host(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
+                    void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!seeds || !pk || !sk) return DIL_EINVAL;
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    uint8_t *d_seed, *d_pk, *d_sk;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard g(c->device);
+        int rc = ensure_stage(c, al(32 * n) + al(pkb * n) + al(skb * n));
+        if (rc) return rc;
+        d_seed = (uint8_t *)c->stage;
+        d_pk = d_seed + al(32 * n);
+        d_sk = d_pk + al(pkb * n);
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d_seed, seeds, 32 * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    int rc = dil_keygen(c, level, n, d_seed, d_pk, d_sk, stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(pk, d_pk, pkb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
+    if (cudaMemcpyAsync(sk, d_sk, skb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
+int dil_sign_host(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
+                  uint8_t *sig, int32_t *task_status, void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!sk || !msg_off || !sig) return DIL_EINVAL;
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    size_t mlen = (size_t)msg_off[n];
+    if (mlen && !msg) return DIL_EINVAL;
+    uint8_t *d_sk, *d_msg, *d_sig;
+    uint64_t *d_off;
+    int32_t *d_st;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard g(c->device);
+        int rc = ensure_stage(c, al(skb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(4 * n));
+        if (rc) return rc;
+        d_sk = (uint8_t *)c->stage;
+        d_msg = d_sk + al(skb * n);
+        d_off = (uint64_t *)(d_msg + al(mlen + 1));
+        d_sig = (uint8_t *)d_off + al(8 * (n + 1));
+        d_st = (int32_t *)(d_sig + al(sigb * n));
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d_sk, sk, skb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    if (mlen && cudaMemcpyAsync(d_msg, msg, mlen, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    if (cudaMemcpyAsync(d_off, msg_off, 8 * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    int rc = dil_sign(c, level, n, d_sk, d_msg, d_off, d_sig, d_st, stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(sig, d_sig, sigb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
+    if (task_status && cudaMemcpyAsync(task_status, d_st, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return DIL_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
+int dil_verify_host(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
+                    const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream) {
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!pk || !msg_off || !sig || !ok) return DIL_EINVAL;
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    size_t mlen = (size_t)msg_off[n];
+    if (mlen && !msg) return DIL_EINVAL;
+    uint8_t *d_pk, *d_msg, *d_sig, *d_ok;
+    uint64_t *d_off;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard g(c->device);
+        int rc = ensure_stage(c, al(pkb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(n));
+        if (rc) return rc;
+        d_pk = (uint8_t *)c->stage;
+        d_msg = d_pk + al(pkb * n);
+        d_off = (uint64_t *)(d_msg + al(mlen + 1));
+        d_sig = (uint8_t *)d_off + al(8 * (n + 1));
+        d_ok = d_sig + al(sigb * n);
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d_pk, pk, pkb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    if (mlen && cudaMemcpyAsync(d_msg, msg, mlen, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    if (cudaMemcpyAsync(d_off, msg_off, 8 * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    if (cudaMemcpyAsync(d_sig, sig, sigb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
+    int rc = dil_verify(c, level, n, d_pk, d_msg, d_off, d_sig, d_ok, stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(ok, d_ok, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
+// ---------------------------------------------------------------- test-only
+#define TEST_PROLOGUE(ctx)                  \
+    if (!(ctx)) return DIL_EINVAL;          \
+    std::lock_guard<std::mutex> lk((ctx)->mu); \
+    DeviceGuard g((ctx)->device);
+
+static int status_of(cudaError_t e) { return e == cudaSuccess ? DIL_OK : cuda_fail(e); }
+
+int dil_test_shake(dil_ctx *c, int kind, size_t n, const uint8_t *in, const uint64_t *in_off, uint8_t *out,
+                   size_t outlen, void *stream) {
+    TEST_PROLOGUE(c)
+    if ((kind != 128 && kind != 256) || n > (size_t)INT32_MAX || outlen > (1u << 20)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!in_off || !out) return DIL_EINVAL;
+    return status_of(dil::launch_test_shake(kind, (int)n, in, in_off, out, (int)outlen, (cudaStream_t)stream));
+}
+
+int dil_test_ntt(dil_ctx *c, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream) {
+    TEST_PROLOGUE(c)
+    if (n > (size_t)INT32_MAX || (n && (!in || !out))) return DIL_EINVAL;
+    return status_of(dil::launch_test_ntt((int)n, in, out, inverse ? 1 : 0, (cudaStream_t)stream));
+}
+
+int dil_test_expand_a(dil_ctx *c, int level, size_t n, const uint8_t *rho, int32_t *ahat, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!rho || !ahat))) return DIL_EINVAL;
+    return status_of(dil::launch_test_expand_a(level, (int)n, rho, ahat, (cudaStream_t)stream));
+}
+
+int dil_test_expand_s(dil_ctx *c, int level, size_t n, const uint8_t *rhop, int32_t *s, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!rhop || !s))) return DIL_EINVAL;
+    return status_of(dil::launch_test_expand_s(level, (int)n, rhop, s, (cudaStream_t)stream));
+}
+
+int dil_test_expand_mask(dil_ctx *c, int level, size_t n, const uint8_t *rhop, const int32_t *kappa, int32_t *y,
+                         void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!rhop || !kappa || !y))) return DIL_EINVAL;
+    return status_of(dil::launch_test_expand_mask(level, (int)n, rhop, kappa, y, (cudaStream_t)stream));
+}
+
+int dil_test_sample_in_ball(dil_ctx *c, int level, size_t n, const uint8_t *ctilde, int32_t *cc, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!ctilde || !cc))) return DIL_EINVAL;
+    return status_of(dil::launch_test_sample_in_ball(level, (int)n, ctilde, cc, (cudaStream_t)stream));
+}
+
+int dil_test_rounding(dil_ctx *c, int level, size_t n, const int32_t *r, const int32_t *z, const uint8_t *h,
+                      int32_t *out, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!r || !z || !h || !out))) return DIL_EINVAL;
+    return status_of(dil::launch_test_rounding(level, (int)n, r, z, h, out, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Kernels behind the test-only entry points: one primitive of the hot path per
+// kernel (SHAKE, NTT/INTT, the four samplers, the coefficient functions), each
+// built from the same device functions the fused procedure kernels use.
+#include "dil_launch.h"
+#include "dil_procs.cuh"
+
+namespace dil {
+
+#define PRIM_PROLOGUE                                                             \
+    extern __shared__ __align__(16) uint8_t smem[];                               \
+    int32_t *zt = reinterpret_cast<int32_t *>(smem);                              \
+    int32_t *izt = zt + 256;                                                      \
+    WarpSmem *wsa = reinterpret_cast<WarpSmem *>(smem + CTA_TABLE_BYTES);         \
+    load_zetas(zt, izt);                                                          \
+    __syncthreads();                                                              \
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;                   \
+    const int item = blockIdx.x * (blockDim.x >> 5) + warp;                       \
+    if (item >= n) return;                                                        \
+    WarpSmem &ws = wsa[warp];                                                     \
+    const KLane k = klane_init(lane);                                             \
+    (void)zt; (void)izt; (void)ws; (void)k;
+
+constexpr int PRIM_WARPS = 4;
+
+__global__ void k_test_shake(int n, int rate, const uint8_t *in, const uint64_t *off, uint8_t *out, int outlen) {
+    PRIM_PROLOGUE
+    uint32_t lo = 0, hi = 0;
+    absorb_concat(lo, hi, k, ws.sq, 0, in + off[item], (size_t)(off[item + 1] - off[item]), rate, lane);
+    uint8_t *o = out + (size_t)item * outlen;
+    for (int p = 0; p < outlen; p += rate) {
+        if (p) keccak_f(lo, hi, k);
+        squeeze_words(lo, hi, ws.sq, rate / 8, lane);
+        __syncwarp();
+        for (int b = lane; b < rate && p + b < outlen; b += 32) o[p + b] = ws.sq[b];
+        __syncwarp();
+    }
+}
+
+__global__ void k_test_ntt(int n, const int32_t *in, int32_t *out, int inverse) {
+    PRIM_PROLOGUE
+    int32_t r[8];
+    const int32_t *src = in + (size_t)item * N;
+    int32_t *dst = out + (size_t)item * N;
+    if (!inverse) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) r[m] = reduce_q(src[lane + 32 * m]);
+        ntt_fwd(r, ws.buf, zt, lane);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) r[m] = to_canonical(reduce_q(r[m]));
+        store_l2(dst, r, lane);
+    } else {
+        // ntt_inv returns INTT(x) * 2^32; feed x * 2^-32 = mont_mul(x, 1)
+        load_l2(r, src, lane);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) r[m] = mont_mul(reduce_q(r[m]), 1);
+        ntt_inv(r, ws.buf, izt, lane);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) r[m] = to_canonical(r[m]);
+        store_l0(dst, r, lane);
+    }
+}
+
+template <int LEVEL>
+__global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    stage_bytes(ws.rho, rho + (size_t)item * 32, 32, lane);
+    __syncwarp();
+    for (int i = 0; i < V::K; ++i)
+        for (int j = 0; j < V::L; ++j) {
+            expand_a_poly(ws.rho, i, j, ws.buf, ws.sq, k, lane);
+            int32_t a[8];
+            read_buf_l2(a, ws.buf, lane);
+            __syncwarp();
+            store_l2(out + ((size_t)item * V::K * V::L + i * V::L + j) * N, a, lane);
+        }
+}
+
+template <int LEVEL>
+__global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    stage_bytes(ws.rhop, rhop + (size_t)item * 64, 64, lane);
+    __syncwarp();
+    for (int j = 0; j < V::L + V::K; ++j) {
+        expand_s_poly<V::ETA>(ws.rhop, j, ws.buf, ws.sq, k, lane);
+        int32_t a[8];
+        read_buf_l0(a, ws.buf, lane);
+        __syncwarp();
+        store_l0(out + ((size_t)item * (V::K + V::L) + j) * N, a, lane);
+    }
+}
+
+template <int LEVEL>
+__global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    stage_bytes(ws.rhop, rhop + (size_t)item * 64, 64, lane);
+    __syncwarp();
+    for (int j = 0; j < V::L; ++j) {
+        int32_t a[8];
+        expand_mask_poly<V::ZBITS, V::GAMMA1>(ws.rhop, kappa[item] + j, a, ws.sq, k, lane);
+        store_l0(out + ((size_t)item * V::L + j) * N, a, lane);
+    }
+}
+
+template <int LEVEL>
+__global__ void k_test_sample_in_ball(int n, const uint8_t *ct, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    stage_bytes(ws.ctilde, ct + (size_t)item * 32, 32, lane);
+    __syncwarp();
+    sample_in_ball<V::TAU>(ws.ctilde, ws.buf, ws.sq, k, lane);
+    int32_t a[8];
+    read_buf_l0(a, ws.buf, lane);
+    store_l0(out + (size_t)item * N, a, lane);
+}
+
+template <int LEVEL>
+__global__ void k_test_rounding(int n, const int32_t *r, const int32_t *z, const uint8_t *h, int32_t *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t v = r[i], a1, a0;
+    int32_t *o = out + (size_t)i * 6;
+    power2round(v, a1, a0);
+    o[0] = a1;
+    o[1] = a0;
+    decompose<LEVEL>(v, a1, a0);
+    o[2] = a1;
+    o[3] = a0;
+    o[4] = make_hint<LEVEL>(z[i], v);
+    o[5] = use_hint<LEVEL>(h[i], v);
+}
+
+template <class Kern, class... Args>
+static cudaError_t launch_prim(Kern kern, int n, cudaStream_t s, Args... args) {
+    if (n <= 0) return cudaSuccess;
+    size_t smem = cta_smem_bytes(PRIM_WARPS);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(n + PRIM_WARPS - 1) / PRIM_WARPS, PRIM_WARPS * 32, smem, s>>>(n, args...);
+    return cudaGetLastError();
+}
+
+#define BY_LEVEL(KERN, ...)                                            \
+    switch (level) {                                                   \
+        case 2: return launch_prim(KERN<2>, n, s, __VA_ARGS__);        \
+        case 3: return launch_prim(KERN<3>, n, s, __VA_ARGS__);        \
+        case 5: return launch_prim(KERN<5>, n, s, __VA_ARGS__);        \
+    }                                                                  \
+    return cudaErrorInvalidValue;
+
+cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t *off, uint8_t *out, int outlen,
+                              cudaStream_t s) {
+    return launch_prim(k_test_shake, n, s, kind == 128 ? 168 : 136, in, off, out, outlen);
+}
+cudaError_t launch_test_ntt(int n, const int32_t *in, int32_t *out, int inverse, cudaStream_t s) {
+    return launch_prim(k_test_ntt, n, s, in, out, inverse);
+}
+cudaError_t launch_test_expand_a(int level, int n, const uint8_t *rho, int32_t *out, cudaStream_t s) {
+    BY_LEVEL(k_test_expand_a, rho, out)
+}
+cudaError_t launch_test_expand_s(int level, int n, const uint8_t *rhop, int32_t *out, cudaStream_t s) {
+    BY_LEVEL(k_test_expand_s, rhop, out)
+}
+cudaError_t launch_test_expand_mask(int level, int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out,
+                                    cudaStream_t s) {
+    BY_LEVEL(k_test_expand_mask, rhop, kappa, out)
+}
+cudaError_t launch_test_sample_in_ball(int level, int n, const uint8_t *ct, int32_t *out, cudaStream_t s) {
+    BY_LEVEL(k_test_sample_in_ball, ct, out)
+}
+cudaError_t launch_test_rounding(int level, int n, const int32_t *r, const int32_t *z, const uint8_t *h,
+                                 int32_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int grid = (n + 255) / 256;
+    switch (level) {
+        case 2: k_test_rounding<2><<<grid, 256, 0, s>>>(n, r, z, h, out); break;
+        case 3: k_test_rounding<3><<<grid, 256, 0, s>>>(n, r, z, h, out); break;
+        case 5: k_test_rounding<5><<<grid, 256, 0, s>>>(n, r, z, h, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dil

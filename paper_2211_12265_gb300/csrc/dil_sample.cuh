@@ -1,0 +1,171 @@
+// Warp-level samplers (section 2.3 "Sampling"; section 3.4 / Alg 4 of
+// arXiv 2211.12265: rejection sampling with a warp vote of the accept bits, an
+// inclusive popcount for each lane's write offset and a running count).
+#pragma once
+#include "dil_keccak.cuh"
+#include "dil_ntt.cuh"
+
+namespace dil {
+
+__device__ __forceinline__ uint32_t lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Upper bound on squeezed blocks in any rejection sampler: the samplers need
+// 1-6 blocks except with negligible probability; the bound only guarantees
+// that no input can make a warp loop forever.
+constexpr int MAX_SQUEEZE_BLOCKS = 64;
+
+// Reads a little-endian field of `bits` (<= 25) bits starting at bit `pos`
+// from a 4-byte-aligned shared buffer readable one word beyond the field.
+__device__ __forceinline__ uint32_t get_field(const uint8_t *buf, int pos, int bits) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(buf);
+    uint32_t v = __funnelshift_r(w[pos >> 5], w[(pos >> 5) + 1], pos & 31);
+    return v & ((1u << bits) - 1u);
+}
+
+// ExpandA: A^_ij from SHAKE128(rho || j || i).  Candidates are 3-byte
+// little-endian words with the top bit cleared, kept when < q, in stream order;
+// coefficient c is written to buf[c + (c >> 3)] (layout for an L2 read).
+// rho: 32 bytes in shared memory (8-byte aligned); sq: >= 176-byte scratch.
+__device__ __forceinline__ void expand_a_poly(const uint8_t *rho, int i, int j, int32_t *buf, uint8_t *sq,
+                                              const KLane &k, int lane) {
+    uint32_t lo, hi;
+    absorb_seed(lo, hi, k, rho, 4, (uint32_t)j | ((uint32_t)i << 8), 2, 168, lane);
+    int ctr = 0;
+    // bounded: a correct stream needs 5 or 6 blocks; 64 is unreachable in practice
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+        squeeze_words(lo, hi, sq, 21, lane);
+        __syncwarp();
+#pragma unroll
+        for (int rnd = 0; rnd < 2; ++rnd) {
+            int c = rnd * 32 + lane;
+            bool valid = c < 56;
+            uint32_t v = valid ? (get_field(sq, 24 * c, 24) & 0x7FFFFFu) : 0u;
+            bool acc = valid && v < (uint32_t)Q;
+            uint32_t mask = __ballot_sync(FULL, acc);
+            int pos = ctr + __popc(mask & lanemask_lt(lane));
+            if (acc && pos < N) buf[pos + (pos >> 3)] = (int32_t)v;
+            ctr += __popc(mask);
+        }
+        __syncwarp();
+        if (ctr >= N) break;
+        keccak_f(lo, hi, k);
+    }
+}
+
+// ExpandS: one polynomial with coefficients in [-eta, eta] from
+// SHAKE256(rho' || nonce); each byte gives two 4-bit candidates, low first.
+// Coefficient c is written to buf[c + 4 (c >> 5)] (layout for an L0 read).
+template <int ETA>
+__device__ __forceinline__ void expand_s_poly(const uint8_t *rhop, int nonce, int32_t *buf, uint8_t *sq,
+                                              const KLane &k, int lane) {
+    uint32_t lo, hi;
+    absorb_seed(lo, hi, k, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
+    int ctr = 0;
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+        squeeze_words(lo, hi, sq, 17, lane);
+        __syncwarp();
+#pragma unroll
+        for (int rnd = 0; rnd < 5; ++rnd) {
+            int c = rnd * 32 + lane;
+            bool valid = c < 136;
+            uint32_t byte = valid ? sq[c] : 0xFFu;
+            uint32_t t0 = byte & 15u, t1 = byte >> 4;
+            bool a0 = valid && (ETA == 2 ? t0 < 15u : t0 < 9u);
+            bool a1 = valid && (ETA == 2 ? t1 < 15u : t1 < 9u);
+            uint32_t m0 = __ballot_sync(FULL, a0), m1 = __ballot_sync(FULL, a1);
+            uint32_t lt = lanemask_lt(lane);
+            int pos0 = ctr + __popc(m0 & lt) + __popc(m1 & lt);
+            int pos1 = pos0 + (a0 ? 1 : 0);
+            if (a0 && pos0 < N) buf[pos0 + 4 * (pos0 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t0 % 5u) : 4 - (int32_t)t0;
+            if (a1 && pos1 < N) buf[pos1 + 4 * (pos1 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t1 % 5u) : 4 - (int32_t)t1;
+            ctr += __popc(m0) + __popc(m1);
+        }
+        __syncwarp();
+        if (ctr >= N) break;
+        keccak_f(lo, hi, k);
+    }
+}
+
+// ExpandMask: y = gamma1 - t for consecutive ZBITS-bit fields t of
+// SHAKE256(rho' || nonce).  Returns the polynomial in layout L0.
+template <int ZBITS, int32_t GAMMA1>
+__device__ __forceinline__ void expand_mask_poly(const uint8_t *rhop, int nonce, int32_t r[8], uint8_t *sq,
+                                                 const KLane &k, int lane) {
+    uint32_t lo, hi;
+    absorb_seed(lo, hi, k, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
+    constexpr int BLOCKS = (N * ZBITS / 8 + 135) / 136;
+#pragma unroll 1
+    for (int blk = 0; blk < BLOCKS; ++blk) {
+        if (blk) keccak_f(lo, hi, k);
+        squeeze_words(lo, hi, sq + 136 * blk, 17, lane);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = GAMMA1 - (int32_t)get_field(sq, ZBITS * (lane + 32 * m), ZBITS);
+    __syncwarp();
+}
+
+// SampleInBall: c with TAU coefficients +-1 from SHAKE256(c~): the first 8
+// bytes give the signs, then for i = 256-TAU .. 255 a byte b <= i is drawn,
+// c_i <- c_b and c_b <- +-1.  Coefficient c is written to buf[c + 4 (c >> 5)].
+template <int TAU>
+__device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *buf, uint8_t *sq, const KLane &k,
+                                               int lane) {
+    uint32_t lo, hi;
+    absorb_seed(lo, hi, k, ctilde, 4, 0u, 0, 136, lane);
+    squeeze_words(lo, hi, sq, 17, lane);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) buf[lane + 36 * m] = 0;
+    __syncwarp();
+    uint64_t signs = *reinterpret_cast<const unsigned long long *>(sq);
+    int pos = 8, blocks = 1;
+    for (int i = N - TAU; i < N; ++i) {
+        int b;
+        do {
+            if (pos == 136) {
+                if (++blocks > MAX_SQUEEZE_BLOCKS) break;
+                __syncwarp();
+                keccak_f(lo, hi, k);
+                squeeze_words(lo, hi, sq, 17, lane);
+                __syncwarp();
+                pos = 0;
+            }
+            b = sq[pos++];
+        } while (b > i);
+        if (lane == 0) {
+            int32_t cb = buf[b + 4 * (b >> 5)];
+            buf[i + 4 * (i >> 5)] = cb;
+            buf[b + 4 * (b >> 5)] = (signs & 1) ? -1 : 1;
+        }
+        signs >>= 1;
+    }
+    __syncwarp();
+}
+
+// Packs 8 consecutive values (each < 2^BITS) into BITS bytes at out
+// (little-endian bit stream).
+template <int BITS>
+__device__ __forceinline__ void pack8(uint8_t *out, const uint32_t v[8]) {
+    uint64_t acc = 0;
+    int nb = 0, o = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        acc |= (uint64_t)v[m] << nb;
+        nb += BITS;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (nb >= 8) {
+                out[o++] = (uint8_t)acc;
+                acc >>= 8;
+                nb -= 8;
+            }
+        }
+    }
+}
+
+// Copies nbytes from global to shared memory, one byte per lane per step.
+__device__ __forceinline__ void stage_bytes(uint8_t *dst, const uint8_t *__restrict__ src, int nbytes, int lane) {
+    for (int i = lane; i < nbytes; i += 32) dst[i] = __ldg(src + i);
+}
+
+}  // namespace dil

@@ -1,0 +1,256 @@
+"""ctypes binding of the C ABI in ``include/dil.h`` (argument marshalling only).
+
+Module-level functions carry the C entry points' names and signatures; device
+buffers may be passed as ``torch.Tensor`` (CUDA, contiguous), as raw integer
+device pointers, or as ``None`` for nullable arguments.  ``Context`` wraps a
+``dil_ctx`` and adds allocating conveniences built on the same calls.
+
+There is no fallback: if ``libdil.so`` cannot be loaded (or built with nvcc),
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EITER = 0, -1, -2, -3, -4, -5
+SIZES = {2: (1312, 2528, 2420), 3: (1952, 4000, 3293), 5: (2592, 4864, 4595)}
+PARAMS = {2: dict(k=4, l=4), 3: dict(k=6, l=5), 5: dict(k=8, l=7)}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DilError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads libdil.so (building it with nvcc when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdil.so missing at {path}")
+            L = ctypes.CDLL(path)
+            P, S, I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+            sigs = {
+                "dil_sizes": [I, P, P, P],
+                "dil_ctx_create": [I, S, P],
+                "dil_ctx_destroy": [P],
+                "dil_set_max_iter": [P, I],
+                "dil_keygen": [P, I, S, P, P, P, P],
+                "dil_sign": [P, I, S, P, P, P, P, P, P],
+                "dil_sign_ex": [P, I, S, P, P, P, P, P, P, P],
+                "dil_verify": [P, I, S, P, P, P, P, P, P],
+                "dil_keygen_host": [P, I, S, P, P, P, P],
+                "dil_sign_host": [P, I, S, P, P, P, P, P, P],
+                "dil_verify_host": [P, I, S, P, P, P, P, P, P],
+                "dil_test_shake": [P, I, S, P, P, P, S, P],
+                "dil_test_ntt": [P, S, P, P, I, P],
+                "dil_test_expand_a": [P, I, S, P, P, P],
+                "dil_test_expand_s": [P, I, S, P, P, P],
+                "dil_test_expand_mask": [P, I, S, P, P, P, P],
+                "dil_test_sample_in_ball": [P, I, S, P, P, P],
+                "dil_test_rounding": [P, I, S, P, P, P, P, P],
+            }
+            for name, args in sigs.items():
+                f = getattr(L, name)
+                f.restype = I
+                f.argtypes = args
+            L.dil_status_string.restype = ctypes.c_char_p
+            L.dil_status_string.argtypes = [I]
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().dil_status_string(status).decode()
+
+
+def _ptr(x):
+    """Device or host address of a tensor / array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != OK:
+        raise DilError(rc, what)
+    return rc
+
+
+# ----------------------------------------------------------------- C names
+def dil_sizes(level: int) -> tuple[int, int, int]:
+    pk, sk, sig = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().dil_sizes(level, ctypes.byref(pk), ctypes.byref(sk), ctypes.byref(sig)), "dil_sizes")
+    return pk.value, sk.value, sig.value
+
+
+def dil_ctx_create(device: int = 0, workspace_budget: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dil_ctx_create(device, workspace_budget, ctypes.byref(h)), "dil_ctx_create")
+    return h.value
+
+
+def dil_ctx_destroy(ctx: int) -> None:
+    _check(load().dil_ctx_destroy(ctx), "dil_ctx_destroy")
+
+
+def dil_set_max_iter(ctx: int, max_iter: int) -> None:
+    _check(load().dil_set_max_iter(ctx, max_iter), "dil_set_max_iter")
+
+
+def dil_keygen(ctx, level, n, seeds, pk, sk, stream=None):
+    return _check(load().dil_keygen(ctx, level, n, _ptr(seeds), _ptr(pk), _ptr(sk), _stream(stream)), "dil_keygen")
+
+
+def dil_sign(ctx, level, n, sk, msg, msg_off, sig, task_status=None, stream=None):
+    return _check(load().dil_sign(ctx, level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                  _ptr(task_status), _stream(stream)), "dil_sign")
+
+
+def dil_sign_ex(ctx, level, n, sk, msg, msg_off, sig, task_status=None, iterations=None, stream=None):
+    return _check(load().dil_sign_ex(ctx, level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                     _ptr(task_status), _ptr(iterations), _stream(stream)), "dil_sign_ex")
+
+
+def dil_verify(ctx, level, n, pk, msg, msg_off, sig, ok, stream=None):
+    return _check(load().dil_verify(ctx, level, n, _ptr(pk), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(ok),
+                                    _stream(stream)), "dil_verify")
+
+
+def dil_keygen_host(ctx, level, n, seeds, pk, sk, stream=None):
+    return _check(load().dil_keygen_host(ctx, level, n, _ptr(seeds), _ptr(pk), _ptr(sk), _stream(stream)),
+                  "dil_keygen_host")
+
+
+def dil_sign_host(ctx, level, n, sk, msg, msg_off, sig, task_status=None, stream=None):
+    return _check(load().dil_sign_host(ctx, level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                       _ptr(task_status), _stream(stream)), "dil_sign_host")
+
+
+def dil_verify_host(ctx, level, n, pk, msg, msg_off, sig, ok, stream=None):
+    return _check(load().dil_verify_host(ctx, level, n, _ptr(pk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                         _ptr(ok), _stream(stream)), "dil_verify_host")
+
+
+def dil_test_shake(ctx, kind, n, inp, in_off, out, outlen, stream=None):
+    return _check(load().dil_test_shake(ctx, kind, n, _ptr(inp), _ptr(in_off), _ptr(out), outlen,
+                                        _stream(stream)), "dil_test_shake")
+
+
+def dil_test_ntt(ctx, n, inp, out, inverse, stream=None):
+    return _check(load().dil_test_ntt(ctx, n, _ptr(inp), _ptr(out), int(inverse), _stream(stream)), "dil_test_ntt")
+
+
+def dil_test_expand_a(ctx, level, n, rho, ahat, stream=None):
+    return _check(load().dil_test_expand_a(ctx, level, n, _ptr(rho), _ptr(ahat), _stream(stream)),
+                  "dil_test_expand_a")
+
+
+def dil_test_expand_s(ctx, level, n, rhop, s, stream=None):
+    return _check(load().dil_test_expand_s(ctx, level, n, _ptr(rhop), _ptr(s), _stream(stream)),
+                  "dil_test_expand_s")
+
+
+def dil_test_expand_mask(ctx, level, n, rhop, kappa, y, stream=None):
+    return _check(load().dil_test_expand_mask(ctx, level, n, _ptr(rhop), _ptr(kappa), _ptr(y), _stream(stream)),
+                  "dil_test_expand_mask")
+
+
+def dil_test_sample_in_ball(ctx, level, n, ctilde, c, stream=None):
+    return _check(load().dil_test_sample_in_ball(ctx, level, n, _ptr(ctilde), _ptr(c), _stream(stream)),
+                  "dil_test_sample_in_ball")
+
+
+def dil_test_rounding(ctx, level, n, r, z, h, out, stream=None):
+    return _check(load().dil_test_rounding(ctx, level, n, _ptr(r), _ptr(z), _ptr(h), _ptr(out),
+                                           _stream(stream)), "dil_test_rounding")
+
+
+# ----------------------------------------------------------------- wrapper
+class Context:
+    """Owns a dil_ctx.  Methods take and return torch CUDA tensors."""
+
+    def __init__(self, device: int = 0, workspace_budget: int = 0):
+        self.device = device
+        self.handle = dil_ctx_create(device, workspace_budget)
+
+    def close(self) -> None:
+        if self.handle:
+            dil_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_max_iter(self, max_iter: int) -> None:
+        dil_set_max_iter(self.handle, max_iter)
+
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.device)
+
+    def keygen(self, level: int, seeds, stream=None):
+        import torch
+        n = seeds.shape[0]
+        pkb, skb, _ = SIZES[level]
+        pk = torch.empty((n, pkb), dtype=torch.uint8, device=self._dev())
+        sk = torch.empty((n, skb), dtype=torch.uint8, device=self._dev())
+        dil_keygen(self.handle, level, n, seeds, pk, sk, stream)
+        return pk, sk
+
+    def sign(self, level: int, sk, msg, msg_off, stream=None, iterations: bool = False):
+        import torch
+        n = sk.shape[0]
+        sig = torch.empty((n, SIZES[level][2]), dtype=torch.uint8, device=self._dev())
+        status = torch.empty(n, dtype=torch.int32, device=self._dev())
+        its = torch.empty(n, dtype=torch.int32, device=self._dev()) if iterations else None
+        dil_sign_ex(self.handle, level, n, sk, msg if msg.numel() else None, msg_off, sig, status, its, stream)
+        return (sig, status, its) if iterations else (sig, status)
+
+    def verify(self, level: int, pk, msg, msg_off, sig, stream=None):
+        import torch
+        n = pk.shape[0]
+        ok = torch.empty(n, dtype=torch.uint8, device=self._dev())
+        dil_verify(self.handle, level, n, pk, msg if msg.numel() else None, msg_off, sig, ok, stream)
+        return ok

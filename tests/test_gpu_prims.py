@@ -1,0 +1,115 @@
+"""Parity of each hot-path primitive (SHAKE, NTT/INTT, samplers, rounding) on
+the GPU against the oracle, bit-exact, through the test-only C entry points."""
+import hashlib
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+Q = 8380417
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2211_12265_gb300 import dil
+    c = dil.Context(0)
+    yield c
+    c.close()
+
+
+def test_shake_lengths(ctx, orc):
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    rng = np.random.default_rng(1)
+    lens = np.concatenate([np.arange(0, 350), [407, 408, 409, 1000, 4096, 16384, 0]])
+    msg = rng.integers(0, 256, int(lens.sum()) + 1, dtype=np.uint8)
+    off = np.zeros(lens.size + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    for kind, outlen in ((128, 840), (256, 700), (256, 32)):
+        out = torch.empty((lens.size, outlen), dtype=torch.uint8, device="cuda")
+        dil.dil_test_shake(ctx.handle, kind, lens.size, dev(msg), dev(off), out, outlen)
+        got = host(out)
+        for i in range(lens.size):
+            m = msg[off[i]:off[i + 1]].tobytes()
+            want = hashlib.shake_128(m).digest(outlen) if kind == 128 else hashlib.shake_256(m).digest(outlen)
+            assert got[i].tobytes() == want, (kind, i, lens[i])
+        assert got[5].tobytes() == (orc.shake128 if kind == 128 else orc.shake256)(msg[off[5]:off[6]].tobytes(), outlen)
+
+
+def test_ntt_forward_and_inverse(ctx, orc):
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    rng = np.random.default_rng(2)
+    n = 300
+    a = rng.integers(0, Q, (n, 256)).astype(np.int32)
+    a[0] = 0
+    a[1] = Q - 1
+    a[2] = rng.integers(-(Q - 1), Q, 256)          # signed representatives
+    out = torch.empty((n, 256), dtype=torch.int32, device="cuda")
+    dil.dil_test_ntt(ctx.handle, n, dev(a), out, 0)
+    f = host(out)
+    for i in range(n):
+        assert np.array_equal(f[i], orc.ntt(a[i] % Q)), i
+    dil.dil_test_ntt(ctx.handle, n, dev(f), out, 1)
+    g = host(out)
+    assert np.array_equal(g, a % Q)
+    for i in range(0, n, 37):
+        assert np.array_equal(g[i], orc.intt(f[i]))
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_samplers(ctx, orc, level):
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    p = orc.params(level)
+    k, l = p["k"], p["l"]
+    rng = np.random.default_rng(level)
+    n = 40
+    rho = rng.integers(0, 256, (n, 32), dtype=np.uint8)
+    rhop = rng.integers(0, 256, (n, 64), dtype=np.uint8)
+    kappa = rng.integers(0, 65536 - l, n).astype(np.int32)
+    kappa[:3] = [0, l, 65536 - l]
+    ct = rng.integers(0, 256, (n, 32), dtype=np.uint8)
+    A = torch.empty((n, k, l, 256), dtype=torch.int32, device="cuda")
+    S = torch.empty((n, l + k, 256), dtype=torch.int32, device="cuda")
+    Y = torch.empty((n, l, 256), dtype=torch.int32, device="cuda")
+    C = torch.empty((n, 256), dtype=torch.int32, device="cuda")
+    dil.dil_test_expand_a(ctx.handle, level, n, dev(rho), A)
+    dil.dil_test_expand_s(ctx.handle, level, n, dev(rhop), S)
+    dil.dil_test_expand_mask(ctx.handle, level, n, dev(rhop), dev(kappa), Y)
+    dil.dil_test_sample_in_ball(ctx.handle, level, n, dev(ct), C)
+    A, S, Y, C = host(A), host(S), host(Y), host(C)
+    for i in range(n):
+        assert np.array_equal(A[i], orc.expand_a(level, rho[i].tobytes())), i
+        s1, s2 = orc.expand_s(level, rhop[i].tobytes())
+        assert np.array_equal(S[i], np.concatenate([s1, s2])), i
+        assert np.array_equal(Y[i], orc.expand_mask(level, rhop[i].tobytes(), int(kappa[i]))), i
+        assert np.array_equal(C[i], orc.sample_in_ball(level, ct[i].tobytes())), i
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_rounding_exhaustive(ctx, orc, level):
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    r = np.arange(Q, dtype=np.int32)
+    rng = np.random.default_rng(level)
+    g2 = orc.params(level)["gamma2"]
+    z = (rng.integers(-g2, g2 + 1, Q) % Q).astype(np.int32)
+    h = rng.integers(0, 2, Q, dtype=np.uint8)
+    out = torch.empty((Q, 6), dtype=torch.int32, device="cuda")
+    dil.dil_test_rounding(ctx.handle, level, Q, dev(r), dev(z), dev(h), out)
+    o = host(out)
+    p1, p0 = orc.power2round(r)
+    d1, d0 = orc.decompose(level, r)
+    assert np.array_equal(o[:, 0], p1) and np.array_equal(o[:, 1], p0)
+    assert np.array_equal(o[:, 2], d1) and np.array_equal(o[:, 3], d0)
+    assert np.array_equal(o[:, 4], orc.make_hint(level, z, r))
+    assert np.array_equal(o[:, 5], orc.use_hint(level, h, r))

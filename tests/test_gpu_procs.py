@@ -1,0 +1,162 @@
+"""Parity of the fused Gen / Sign / Verify kernels against the oracle: keys,
+signatures and accept bits bit-exact on the same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2211_12265_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2211_12265_gb300 import dil
+    c = dil.Context(0)
+    yield c
+    c.close()
+
+
+def _batch(orc, level, n, config, kind="fixed", lo=32, hi=32):
+    seeds = W.seeds(n, config)
+    lens = W.message_lengths(n, config, kind, lo, hi)
+    msg, off = W.messages(lens, config)
+    return seeds, msg, off
+
+
+def test_config1_dilithium2_1024_bit_exact(ctx, orc):
+    """Dilithium2, 1024 tasks, 32-byte seeds and 32-byte messages: pk, sk,
+    signatures and accept bits equal the oracle's byte for byte."""
+    from gpu_util import gpu_keygen, gpu_sign, gpu_verify
+    level, n = 2, 1024
+    seeds, msg, off = _batch(orc, level, n, 1)
+    pk, sk = gpu_keygen(ctx, level, seeds)
+    opk, osk = orc.keygen_batch(level, seeds)
+    assert np.array_equal(pk, opk) and np.array_equal(sk, osk)
+    sig, st, it = gpu_sign(ctx, level, sk, msg, off)
+    osig, ost, oit = orc.sign_batch(level, osk, msg, off)
+    assert np.array_equal(st, ost) and np.array_equal(it, oit)
+    assert np.array_equal(sig, osig)
+    ok = gpu_verify(ctx, level, pk, msg, off, sig)
+    assert ok.all()
+
+
+@pytest.mark.parametrize("level", [3, 5])
+def test_levels_3_5_ragged_messages(ctx, orc, level):
+    from gpu_util import gpu_keygen, gpu_sign, gpu_verify
+    n = 200
+    seeds, msg, off = _batch(orc, level, n, 3, "uniform", 0, 4096)
+    pk, sk = gpu_keygen(ctx, level, seeds)
+    opk, osk = orc.keygen_batch(level, seeds)
+    assert np.array_equal(pk, opk) and np.array_equal(sk, osk)
+    sig, st, it = gpu_sign(ctx, level, sk, msg, off)
+    osig, ost, oit = orc.sign_batch(level, osk, msg, off)
+    assert np.array_equal(it, oit) and np.array_equal(sig, osig)
+    assert gpu_verify(ctx, level, pk, msg, off, sig).all()
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_verify_rejections_match_oracle(ctx, orc, level):
+    """Tampered signatures, keys and messages (and malformed hints) are
+    rejected exactly as the oracle rejects them."""
+    from gpu_util import gpu_verify
+    rng = np.random.default_rng(10 + level)
+    seeds, msg, off = _batch(orc, level, 16, 4)
+    pk, sk = orc.keygen_batch(level, seeds)
+    sig, _, _ = orc.sign_batch(level, sk, msg, off)
+    reps = 24
+    P = np.repeat(pk, reps, axis=0)
+    S = np.repeat(sig, reps, axis=0)
+    M = np.concatenate([msg[off[i]:off[i + 1]] for i in range(16) for _ in range(reps)])
+    O = np.arange(16 * reps + 1, dtype=np.uint64) * 32
+    for t in range(16 * reps):
+        kind = t % reps
+        if kind == 0:
+            continue                                   # untouched
+        if kind < 10:                                  # signature bit
+            b = rng.integers(0, S.shape[1] * 8)
+            S[t, b // 8] ^= 1 << (b % 8)
+        elif kind < 14:                                # hint region byte
+            p = orc.params(level)
+            start = S.shape[1] - p["omega"] - p["k"]
+            S[t, start + rng.integers(0, p["omega"] + p["k"])] ^= 1 << rng.integers(0, 8)
+        elif kind < 19:                                # public-key bit
+            b = rng.integers(0, P.shape[1] * 8)
+            P[t, b // 8] ^= 1 << (b % 8)
+        else:                                          # message bit
+            M[32 * t + rng.integers(0, 32)] ^= 1 << rng.integers(0, 8)
+    ok = gpu_verify(ctx, level, P, M, O, S)
+    want = orc.verify_batch(level, P, M, O, S)
+    assert np.array_equal(ok, want)
+    assert ok[::reps].all() and ok.sum() == 16
+
+
+def test_empty_and_single(ctx, orc):
+    import torch
+    from gpu_util import dev, gpu_keygen, gpu_sign, gpu_verify
+    from paper_2211_12265_gb300 import dil
+    level = 2
+    # n = 0 is a no-op
+    dil.dil_keygen(ctx.handle, level, 0, None, None, None)
+    seeds = W.seeds(1, 7)
+    pk, sk = gpu_keygen(ctx, level, seeds)
+    msg = np.zeros(1, dtype=np.uint8)
+    off = np.zeros(2, dtype=np.uint64)                 # one empty message
+    sig, st, _ = gpu_sign(ctx, level, sk, msg, off)
+    osig, ost, _ = orc.sign_batch(level, sk, msg, off)
+    assert np.array_equal(sig, osig) and st[0] == 0
+    assert gpu_verify(ctx, level, pk, msg, off, sig)[0] == 1
+
+
+def test_iteration_cap(ctx, orc):
+    from gpu_util import gpu_sign
+    level = 2
+    seeds, msg, off = _batch(orc, level, 128, 6)
+    _, sk = orc.keygen_batch(level, seeds)
+    ctx.set_max_iter(1)
+    try:
+        sig, st, it = gpu_sign(ctx, level, sk, msg, off)
+    finally:
+        ctx.set_max_iter(0)
+    osig, ost, oit = orc.sign_batch(level, sk, msg, off, max_iter=1)
+    assert np.array_equal(st, ost) and np.array_equal(sig, osig) and np.array_equal(it, oit)
+    assert (st == -5).any() and (st == 0).any()
+
+
+def test_chunked_launches_match(orc):
+    """A workspace budget smaller than the batch forces several launches; the
+    output is unchanged."""
+    from gpu_util import gpu_sign
+    from paper_2211_12265_gb300 import dil
+    level = 5
+    seeds, msg, off = _batch(orc, level, 100, 8)
+    _, sk = orc.keygen_batch(level, seeds)
+    small = dil.Context(0, workspace_budget=13 * 108 * 1024)   # 13 tasks per launch
+    try:
+        sig, st, _ = gpu_sign(small, level, sk, msg, off)
+    finally:
+        small.close()
+    osig, ost, _ = orc.sign_batch(level, sk, msg, off)
+    assert np.array_equal(sig, osig) and np.array_equal(st, ost)
+
+
+def test_host_forms_match_device_forms(ctx, orc):
+    from paper_2211_12265_gb300 import dil
+    level = 3
+    seeds, msg, off = _batch(orc, level, 64, 9, "uniform", 0, 300)
+    pkb, skb, sigb = dil.SIZES[level]
+    pk = np.zeros((64, pkb), np.uint8)
+    sk = np.zeros((64, skb), np.uint8)
+    dil.dil_keygen_host(ctx.handle, level, 64, seeds, pk, sk)
+    opk, osk = orc.keygen_batch(level, seeds)
+    assert np.array_equal(pk, opk) and np.array_equal(sk, osk)
+    sig = np.zeros((64, sigb), np.uint8)
+    st = np.zeros(64, np.int32)
+    dil.dil_sign_host(ctx.handle, level, 64, sk, msg, off, sig, st)
+    osig, _, _ = orc.sign_batch(level, osk, msg, off)
+    assert np.array_equal(sig, osig)
+    ok = np.zeros(64, np.uint8)
+    dil.dil_verify_host(ctx.handle, level, 64, pk, msg, off, sig, ok)
+    assert ok.all()
