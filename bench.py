@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched Dilithium engine on GB300.
+
+Default workload (one "step"): Dilithium2, 10,000 independent tasks with
+distinct seeded key pairs and 32-byte messages; Sign of the whole batch (one
+launch) followed by Verify of the resulting signatures (one launch), plain
+one-launch-per-phase form.  Inputs are resident in HBM when timing starts and
+L2 is flushed (512 MiB write) before every step.  ``value`` is
+(signs + verifies) per second over all ranks; ``e2e`` is the same through the
+host-buffer C entry points with the copies inside the timed region.
+
+Other workloads: ``--workload level3|level5`` (config 3 of the paper-derived
+benchmark set: 10,000 tasks, messages of 32..4096 bytes).
+
+``--impl reference`` times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.
+
+Multi-GPU: tasks are independent, so N ranks run N replicas of the workload
+(weak scaling, no collective on the data path); the step time is the maximum
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_12265_gb300 import work as WK  # noqa: E402
+from paper_2211_12265_gb300 import workload as W  # noqa: E402
+
+METRIC = "Dilithium2/3/5 sign & verify ops/s on 1 GB300; served p50/p99 latency"
+PAPER_A100 = {2: {"sign_ops_s": 574953, "verify_ops_s": 1408703},
+              3: {"sign_ops_s": 396360, "verify_ops_s": 982648},
+              5: {"sign_ops_s": 315900, "verify_ops_s": 637299}}
+SMS = 152
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "level2": dict(level=2, n=10000, config=2),
+    "level3": dict(level=3, n=10000, config=3),
+    "level5": dict(level=5, n=10000, config=3),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="level2")
+    ap.add_argument("--n", type=int, default=0, help="override the task count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- ranks
+class Ranks:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.samples = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [s for t, s in self.samples if self.t0 and self.t1 and self.t0 <= t <= self.t1 + 0.2]
+        if not rows:
+            rows = [s for _, s in self.samples]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle
+def cpu_baseline(level: int, wl: dict, budget_s: float = 15.0) -> dict:
+    """Times the CPU oracle (as it stands) on a bounded sample of the workload:
+    Sign then Verify of `sample` tasks on all host cores."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    n_all = wl["seeds"].shape[0]
+    # keys for the sample are generated outside the timed region
+    sample = min(n_all, max(cores * 4, 64))
+    seeds = wl["seeds"][:sample]
+    lens = wl["lengths"][:sample]
+    off = wl["msg_off"][: sample + 1]
+    msg = wl["msg"][: int(off[-1]) + 1]
+    pk, sk = oracle.keygen_batch(level, seeds, nthreads=cores)
+    done, t_total = 0, 0.0
+    while t_total < budget_s:
+        t0 = time.perf_counter()
+        sig, st, _ = oracle.sign_batch(level, sk, msg, off, nthreads=cores)
+        ok = oracle.verify_batch(level, pk, msg, off, sig, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        done += sample
+        assert ok.all()
+    return {"value": 2 * done / t_total, "unit": "ops/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} Dilithium{level} sign+verify tasks ({sample} distinct, messages "
+                      f"{int(lens.min())}-{int(lens.max())} B) in {t_total:.1f} s"}
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args, ranks: Ranks) -> dict | None:
+    import torch
+
+    from paper_2211_12265_gb300 import dil
+
+    spec = WORKLOADS[args.workload]
+    level, n = spec["level"], (args.n or spec["n"])
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    wl = W.workload(spec["config"], n)
+    # per-rank replicas draw distinct keys
+    if ranks.rank:
+        wl["seeds"] = W.seeds(n, spec["config"], offset=ranks.rank * n)
+    ctx = dil.Context(dev)
+    seeds = torch.from_numpy(wl["seeds"]).cuda()
+    msg = torch.from_numpy(wl["msg"]).cuda()
+    off = torch.from_numpy(wl["msg_off"]).cuda()
+    pk, sk = ctx.keygen(level, seeds)                     # untimed key generation
+    sig, status, its = ctx.sign(level, sk, msg, off, iterations=True)
+    ok = ctx.verify(level, pk, msg, off, sig)
+    torch.cuda.synchronize()
+    assert bool((status == 0).all()) and bool(ok.all()), "warm-up batch failed"
+    iters = its.cpu().numpy()
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    n_ops = 2 * n
+
+    def step(ev):
+        flush.fill_(1)                                   # evict L2 between steps
+        ev[0].record(stream)
+        dil.dil_sign(ctx.handle, level, n, sk, msg, off, sig, status, stream)
+        ev[1].record(stream)
+        dil.dil_verify(ctx.handle, level, n, pk, msg, off, sig, ok, stream)
+        ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clk = ClockSampler(dev)
+    clk.start()
+    time.sleep(0.5)
+    ranks.barrier()
+    torch.cuda.synchronize()
+    clk.mark(True)
+    wall0 = time.perf_counter()
+    for ev in events:
+        step(ev)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    ranks.barrier()
+    clk.mark(False)
+    clocks = clk.stop()
+    sign_ms = [e[0].elapsed_time(e[1]) for e in events]
+    ver_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = float(np.mean(np.add(sign_ms, ver_ms)))
+    step_ms_max = ranks.max(step_ms)
+    assert bool((status == 0).all()) and bool(ok.all())
+
+    # e2e: host buffers through the host-form C entry points
+    h_sk = torch.empty_like(sk, device="cpu").pin_memory()
+    h_sk.copy_(sk)
+    h_pk = torch.empty_like(pk, device="cpu").pin_memory()
+    h_pk.copy_(pk)
+    h_msg = torch.from_numpy(wl["msg"]).pin_memory()
+    h_off = torch.from_numpy(wl["msg_off"]).pin_memory()
+    h_sig = torch.empty(sig.shape, dtype=torch.uint8).pin_memory()
+    h_st = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_ok = torch.empty(n, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(1, min(args.steps, 50))
+
+    def e2e_step():
+        dil.dil_sign_host(ctx.handle, level, n, h_sk, h_msg, h_off, h_sig, h_st, stream)
+        dil.dil_verify_host(ctx.handle, level, n, h_pk, h_msg, h_off, h_sig, h_ok, stream)
+
+    for _ in range(2):
+        e2e_step()
+    ranks.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = ranks.max((time.perf_counter() - t0) * 1e3 / e2e_steps)
+    assert bool((h_st == 0).all()) and bool(h_ok.all())
+    mlen = int(wl["msg_off"][-1])
+    h2d = sk.numel() + mlen + 8 * (n + 1) + pk.numel() + mlen + 8 * (n + 1) + sig.numel()
+    d2h = sig.numel() + 4 * n + n
+
+    # roofline of the dominant kernel (Sign): algorithmic integer ops / its time
+    sw = WK.sign_work(level, iters, wl["lengths"])
+    ops = WK.int_ops(sw)
+    sign_mean_ms = float(np.mean(sign_ms))
+    achieved = ops / (sign_mean_ms * 1e-3) / 1e12
+    lop3_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["lop3"])   # thread-ops / SM / clk
+    shfl_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["shfl"])
+    peak = SMS * lop3_rate * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = load_traffic(level, n)
+
+    res = {
+        "metric": METRIC,
+        "value": ranks.world * n_ops / (step_ms_max * 1e-3),
+        "unit": "ops/s",
+        "n_gpus": ranks.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded PCG64 keys and messages)",
+        "config": {"workload": f"dilithium{level}-sign+verify-{n}", "level": level, "n_tasks_per_gpu": n,
+                   "msg_bytes": f"{int(wl['lengths'].min())}-{int(wl['lengths'].max())}",
+                   "form": "plain, one launch per phase", "l2": "flushed before every step (512 MiB write)",
+                   "parallelism": f"replicas x{ranks.world}"},
+        "breakdown": {"sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
+                      "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),
+                      "sign_ms": sign_mean_ms, "verify_ms": float(np.mean(ver_ms)),
+                      "mean_sign_repetitions": float(iters.mean()),
+                      "wall_s_timed_region": wall},
+        "e2e": {"value": ranks.world * n_ops / (e2e_ms * 1e-3), "unit": "ops/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "kernel": f"k_sign<{level}>", "achieved": achieved,
+                     "peak": peak, "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
+                     "traffic": traffic, "ops_per_sign": ops / n,
+                     "peak_basis": f"{SMS} SMs x {lop3_rate:.1f} LOP3 thread-ops/SM/clk (measured live) x "
+                                   f"{SM_MAX_MHZ:.0f} MHz max SM clock",
+                     "shfl_thread_ops_per_sm_clk": shfl_rate},
+        "clocks": clocks,
+        "paper_context_a100": PAPER_A100[level],
+    }
+    ctx.close()
+    if ranks.rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(level, wl)
+    return res
+
+
+def load_traffic(level: int, n: int):
+    """DRAM bytes per Sign launch, scaled from the committed ncu capture of a
+    smaller batch; None when the kernel sources changed since the capture."""
+    from paper_2211_12265_gb300 import build
+    path = os.path.join(ROOT, "profiles", f"k_sign_level{level}_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_digest") != build.source_digest():
+            return None
+        return d["dram_bytes_per_task"] * n
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_reference(args, ranks: Ranks) -> dict | None:
+    if ranks.rank != 0:
+        return None
+    from oracle import oracle
+    spec = WORKLOADS[args.workload]
+    level = spec["level"]
+    cores = os.cpu_count() or 1
+    sample = max(cores * 2, 32)
+    wl = W.workload(spec["config"], sample)
+    pk, sk = oracle.keygen_batch(level, wl["seeds"], nthreads=cores)
+    off, msg = wl["msg_off"], wl["msg"]
+
+    def step():
+        sig, st, _ = oracle.sign_batch(level, sk, msg, off, nthreads=cores)
+        ok = oracle.verify_batch(level, pk, msg, off, sig, nthreads=cores)
+        assert ok.all()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = 2 * sample * args.steps / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ops/s", "n_gpus": ranks.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded PCG64 keys and messages)",
+        "config": {"workload": f"dilithium{level}-sign+verify-{spec['n']}", "level": level,
+                   "n_tasks_per_step": sample, "form": "CPU oracle (plain C, -O2) on host threads"},
+        "cpu_baseline": {"value": value, "unit": "ops/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} tasks per step x {args.steps} steps"},
+        "e2e": {"value": value, "unit": "ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    ranks = Ranks()
+    try:
+        res = run_reference(args, ranks) if args.impl == "reference" else run_ours(args, ranks)
+        if res is not None and ranks.rank == 0:
+            print(json.dumps(res), flush=True)
+    finally:
+        ranks.close()
+
+
+if __name__ == "__main__":
+    main()

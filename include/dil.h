@@ -127,6 +127,13 @@ int dil_test_sample_in_ball(dil_ctx *ctx, int level, size_t n, const uint8_t *ct
 int dil_test_rounding(dil_ctx *ctx, int level, size_t n, const int32_t *r, const int32_t *z,
                       const uint8_t *h, int32_t *out, void *stream);
 
+/* Sustained issue rate of one integer instruction class on the current GPU,
+ * in thread-operations per SM clock (clock64 over independent dependency
+ * chains at full occupancy; synchronous, allocates and frees its buffers).
+ * op: 0 = LOP3, 1 = funnel shift, 2 = 32-bit multiply (low), 3 = multiply
+ * (high, signed), 4 = warp shuffle.  Used for the integer roofline. */
+int dil_test_issue_rate(dil_ctx *ctx, int op, double *thread_ops_per_sm_clk);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,18 @@ def _deps() -> list[str]:
     return out
 
 
+def source_digest(unit: str = "dil_ops.cu") -> str:
+    """SHA-256 over one kernel translation unit and the device headers it
+    includes (ties a committed profile to the kernel version it measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith(".cuh") or f == unit:
+            h.update(f.encode())
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True

@@ -389,4 +389,10 @@ int dil_test_rounding(dil_ctx *c, int level, size_t n, const int32_t *r, const i
     return status_of(dil::launch_test_rounding(level, (int)n, r, z, h, out, (cudaStream_t)stream));
 }
 
+int dil_test_issue_rate(dil_ctx *c, int op, double *thread_ops_per_sm_clk) {
+    TEST_PROLOGUE(c)
+    if (op < 0 || op > 4 || !thread_ops_per_sm_clk) return DIL_EINVAL;
+    return status_of(dil::measure_issue_rate(op, thread_ops_per_sm_clk));
+}
+
 }  // extern "C"

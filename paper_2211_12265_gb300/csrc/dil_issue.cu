@@ -1,0 +1,82 @@
+// Test-only probe behind dil_test_issue_rate: sustained issue rate of one
+// integer instruction class, in thread-operations per SM clock, measured with
+// clock64() over independent dependency chains at full occupancy.  It gives
+// the denominator of the integer roofline the benchmark reports.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "dil_launch.h"
+
+namespace dil {
+
+constexpr int PROBE_ITERS = 4096;
+
+template <int OP>
+__device__ __forceinline__ uint32_t probe_op(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    if (OP == 0) asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    if (OP == 1) asm volatile("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    if (OP == 2) asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    if (OP == 3) asm volatile("mul.hi.s32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    if (OP == 4) r = __shfl_sync(0xffffffffu, a, b & 31);
+    return r;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(1024) k_probe(uint32_t *out, long long *cyc) {
+    uint32_t a0 = threadIdx.x, a1 = a0 * 3 + 1, a2 = a0 * 5 + 2, a3 = a0 * 7 + 3;
+    uint32_t a4 = a0 ^ 9, a5 = a0 + 11, a6 = a0 * 13, a7 = a0 + 17, c = blockIdx.x | 1;
+    __syncthreads();
+    long long t0 = clock64();
+#pragma unroll 4
+    for (int i = 0; i < PROBE_ITERS; ++i) {
+        a0 = probe_op<OP>(a0, a1, c); a1 = probe_op<OP>(a1, a2, c);
+        a2 = probe_op<OP>(a2, a3, c); a3 = probe_op<OP>(a3, a4, c);
+        a4 = probe_op<OP>(a4, a5, c); a5 = probe_op<OP>(a5, a6, c);
+        a6 = probe_op<OP>(a6, a7, c); a7 = probe_op<OP>(a7, a0, c);
+    }
+    __syncthreads();
+    long long t1 = clock64();
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+}
+
+cudaError_t measure_issue_rate(int op, double *rate) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = 2 * sms, threads = 1024;   // two resident 1024-thread blocks per SM
+    uint32_t *out = nullptr;
+    long long *cyc = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 4);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&cyc, (size_t)blocks * 8);
+    if (e != cudaSuccess) {
+        cudaFree(out);
+        return e;
+    }
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        switch (op) {
+            case 0: k_probe<0><<<blocks, threads>>>(out, cyc); break;
+            case 1: k_probe<1><<<blocks, threads>>>(out, cyc); break;
+            case 2: k_probe<2><<<blocks, threads>>>(out, cyc); break;
+            case 3: k_probe<3><<<blocks, threads>>>(out, cyc); break;
+            default: k_probe<4><<<blocks, threads>>>(out, cyc); break;
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    std::vector<long long> h(blocks);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return e;
+    double mean = 0;
+    for (long long v : h) mean += (double)v;
+    mean /= blocks;
+    *rate = 2.0 * threads * PROBE_ITERS * 8 / mean;
+    return cudaSuccess;
+}
+
+}  // namespace dil

@@ -35,4 +35,7 @@ cudaError_t launch_test_sample_in_ball(int level, int n, const uint8_t *ct, int3
 cudaError_t launch_test_rounding(int level, int n, const int32_t *r, const int32_t *z, const uint8_t *h,
                                  int32_t *out, cudaStream_t s);
 
+// test-only issue-rate probe (thread-ops per SM clock)
+cudaError_t measure_issue_rate(int op, double *rate);
+
 }  // namespace dil

@@ -65,6 +65,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_expand_mask": [P, I, S, P, P, P, P],
                 "dil_test_sample_in_ball": [P, I, S, P, P, P],
                 "dil_test_rounding": [P, I, S, P, P, P, P, P],
+                "dil_test_issue_rate": [P, I, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -196,6 +197,16 @@ def dil_test_sample_in_ball(ctx, level, n, ctilde, c, stream=None):
 def dil_test_rounding(ctx, level, n, r, z, h, out, stream=None):
     return _check(load().dil_test_rounding(ctx, level, n, _ptr(r), _ptr(z), _ptr(h), _ptr(out),
                                            _stream(stream)), "dil_test_rounding")
+
+
+def dil_test_issue_rate(ctx, op: int) -> float:
+    """Thread-ops per SM clock of one integer instruction class (see dil.h)."""
+    r = ctypes.c_double()
+    _check(load().dil_test_issue_rate(ctx, op, ctypes.byref(r)), "dil_test_issue_rate")
+    return r.value
+
+
+ISSUE_OPS = {"lop3": 0, "shf": 1, "imul": 2, "imul_hi": 3, "shfl": 4}
 
 
 # ----------------------------------------------------------------- wrapper
