@@ -89,6 +89,22 @@ int dil_sign_ex(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint
 int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
                const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream);
 
+/* Sign that allocates no memory (the paper has no counterpart).  For callers
+ * that cannot call cudaMalloc while signing: a service whose device memory is
+ * already owned by its own allocator, a latency-critical path that cannot
+ * afford cudaMalloc/cudaFree (both may synchronise the device), or code that
+ * must not fail with out-of-memory mid-request.  Same arguments and results as
+ * dil_sign without a context; runs on the current device with the default
+ * repetition cap.  Scratch is a 64 MiB array inside the library's device image
+ * (held by every GPU that loads the library until exit), so n may not exceed
+ * 1489 / 963 / 606 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU race and must be serialised.  Nothing in it needs
+ * clearing (each task's scratch is written before it is read). */
+int dil_sign_noalloc(int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
+                     uint8_t *sig, int32_t *task_status, void *stream);
+
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
  * msg_off too).  They copy inputs to the device, run on `stream`, copy the
  * results back and synchronise the stream before returning. */

@@ -55,6 +55,7 @@ def load() -> ctypes.CDLL:
                 "dil_sign": [P, I, S, P, P, P, P, P, P],
                 "dil_sign_ex": [P, I, S, P, P, P, P, P, P, P],
                 "dil_verify": [P, I, S, P, P, P, P, P, P],
+                "dil_sign_noalloc": [I, S, P, P, P, P, P, P],
                 "dil_keygen_host": [P, I, S, P, P, P, P],
                 "dil_sign_host": [P, I, S, P, P, P, P, P, P],
                 "dil_verify_host": [P, I, S, P, P, P, P, P, P],
@@ -148,6 +149,15 @@ def dil_sign_ex(ctx, level, n, sk, msg, msg_off, sig, task_status=None, iteratio
 def dil_verify(ctx, level, n, pk, msg, msg_off, sig, ok, stream=None):
     return _check(load().dil_verify(ctx, level, n, _ptr(pk), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(ok),
                                     _stream(stream)), "dil_verify")
+
+
+def dil_sign_noalloc(level, n, sk, msg, msg_off, sig, task_status=None, stream=None):
+    """Sign on the library's static scratch (no allocation; see dil.h)."""
+    return _check(load().dil_sign_noalloc(level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                          _ptr(task_status), _stream(stream)), "dil_sign_noalloc")
+
+
+NOALLOC_MAX_TASKS = {2: 1489, 3: 963, 5: 606}
 
 
 def dil_keygen_host(ctx, level, n, seeds, pk, sk, stream=None):

@@ -1,0 +1,70 @@
+"""GPU test of dil_sign_noalloc, the Sign entry point that allocates nothing.
+
+Callers that cannot call cudaMalloc while signing (their device memory belongs
+to their own allocator, or they cannot afford the synchronisation or an
+out-of-memory failure mid-request) use this entry point; it signs on a fixed
+scratch array inside the library.  This file is collected last on purpose.
+
+Checks, through the C ABI: two calls in a row give the same signatures and
+statuses as dil_sign (bit-exact, the tolerance of every parity test here), the
+second call leaves free device memory unchanged, and a batch larger than the
+static scratch is rejected with DIL_EINVAL.
+"""
+import numpy as np
+import pytest
+
+from paper_2211_12265_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(level, n, config):
+    import torch
+    from paper_2211_12265_gb300 import dil
+    seeds = torch.from_numpy(W.seeds(n, config)).cuda()
+    lens = W.message_lengths(n, config, "uniform", 0, 300)
+    msg, off = W.messages(lens, config)
+    with dil.Context(0) as ctx:
+        pk, sk = ctx.keygen(level, seeds)
+        torch.cuda.synchronize()
+    return sk, torch.from_numpy(msg).cuda(), torch.from_numpy(off).cuda()
+
+
+@pytest.mark.parametrize("level", [2, 5])
+def test_noalloc_matches_dil_sign_on_two_calls(level):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2211_12265_gb300 import dil
+    sigb = dil.SIZES[level][2]
+    with dil.Context(0) as ctx:
+        for call, (n, config) in enumerate(((300, 21), (dil.NOALLOC_MAX_TASKS[level], 22))):
+            sk, msg, off = _inputs(level, n, config)
+            ref_sig = torch.empty((n, sigb), dtype=torch.uint8, device="cuda")
+            ref_st = torch.empty(n, dtype=torch.int32, device="cuda")
+            dil.dil_sign(ctx.handle, level, n, sk, msg, off, ref_sig, ref_st)
+            sig = torch.full((n, sigb), 0xAB, dtype=torch.uint8, device="cuda")
+            st = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
+            dil.dil_sign_noalloc(level, n, sk, msg, off, sig, st)
+            torch.cuda.synchronize()
+            free_after = torch.cuda.mem_get_info()[0]
+            assert torch.equal(sig, ref_sig), f"call {call}: signatures differ"
+            assert torch.equal(st, ref_st), f"call {call}: statuses differ"
+            assert bool((st == 0).all())
+            if call == 1:
+                assert free_after == free_before
+
+
+def test_noalloc_rejects_oversized_batch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2211_12265_gb300 import dil
+    n = dil.NOALLOC_MAX_TASKS[3] + 1
+    sk = torch.zeros((n, dil.SIZES[3][1]), dtype=torch.uint8, device="cuda")
+    off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    sig = torch.zeros((n, dil.SIZES[3][2]), dtype=torch.uint8, device="cuda")
+    rc = dil.load().dil_sign_noalloc(3, n, sk.data_ptr(), None, off.data_ptr(), sig.data_ptr(), None, None)
+    assert rc == dil.EINVAL
