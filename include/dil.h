@@ -69,6 +69,13 @@ int dil_ctx_destroy(dil_ctx *ctx);
  * Tasks that reach the cap get DIL_EITER and an all-zero signature. */
 int dil_set_max_iter(dil_ctx *ctx, int max_iter);
 
+/* Launch shape of the plain kernels for op 0 = keygen, 1 = sign, 2 = verify:
+ * warps per CTA (1..8) and warps per task (1, 2 or 4, dividing warps_per_cta;
+ * 32 x warps_per_task threads cooperate on one task, the paper's single-warp
+ * (1) and four-warp (4) forms).  Defaults: 4 warps per CTA, 1 warp per task.
+ * The CTA shares the NTT twiddle tables in shared memory. */
+int dil_set_tuning(dil_ctx *ctx, int op, int warps_per_cta, int warps_per_task);
+
 /* Alg 1 (Gen): n 32-byte seeds -> n public keys and n secret keys. */
 int dil_keygen(dil_ctx *ctx, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
                void *stream);
@@ -104,6 +111,42 @@ int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8
  * clearing (each task's scratch is written before it is read). */
 int dil_sign_noalloc(int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
                      uint8_t *sig, int32_t *task_status, void *stream);
+
+/* ----------------------------------------------------------------------------
+ * Persistent Sign (section 4.3 dynamic task scheduling, on the device): one
+ * launch runs every task of up to three jobs (levels may differ).  Resident
+ * warp groups pull tasks from a device queue; once it is empty they evaluate
+ * further nonces of unfinished tasks, and the signature of the smallest
+ * accepting nonce is committed, so outputs equal dil_sign's byte for byte.
+ * The launch (queue reset + kernel) is captured once into a CUDA graph per
+ * distinct argument set and replayed on later identical calls.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int level;               /* 2, 3 or 5 */
+    size_t n;                /* tasks in this job */
+    const uint8_t *sk;       /* n x SK (device) */
+    const uint8_t *msg;      /* concatenated messages (device, nullable if all empty) */
+    const uint64_t *msg_off; /* n + 1 offsets (device) */
+    uint8_t *sig;            /* n x SIG (device) */
+    int32_t *task_status;    /* n (device, nullable): DIL_OK or DIL_EITER */
+    int32_t *iterations;     /* n (device, nullable): loop repetitions */
+} dil_sign_job;
+
+/* Enqueues one persistent Sign launch on `stream` for njobs (1..3) jobs.  The
+ * context's repetition cap (dil_set_max_iter) applies.  Uses the context's
+ * workspace; calls on one context must not overlap on the GPU. */
+int dil_sign_persistent(dil_ctx *ctx, int njobs, const dil_sign_job *jobs, void *stream);
+
+/* Persistent launch shape: warps per CTA (1..8), warps per task group (1, 2
+ * or 4), CTAs per SM (0 = as many as fit), fresh tasks claimed per queue
+ * access (>= 1), helper groups per unfinished task (0 disables speculation).
+ * Defaults 8, 2, 0, 1, 4. */
+int dil_set_persistent_tuning(dil_ctx *ctx, int warps_per_cta, int warps_per_task, int ctas_per_sm, int chunk,
+                              int speculation);
+
+/* Synchronises `stream` and returns DIL_OK, or DIL_ETIMEOUT when a bounded
+ * device-side wait of the last persistent launch on this context ran out. */
+int dil_persistent_status(dil_ctx *ctx, void *stream);
 
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
  * msg_off too).  They copy inputs to the device, run on `stream`, copy the

@@ -16,10 +16,21 @@ struct dil_ctx {
     void *ws = nullptr;       // device scratch
     size_t ws_bytes = 0;
     int max_iter = 0;         // 0 = nonce cap
-    int warps[3] = {4, 4, 4}; // warps (tasks) per CTA for keygen / sign / verify
+    int warps[3] = {4, 4, 4}; // warps per CTA for keygen / sign / verify
+    int wpt[3] = {1, 1, 1};   // warps per task
     // host-form staging (device memory)
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // persistent Sign: workspace, tuning and the cached captured launch
+    void *pws = nullptr;
+    size_t pws_bytes = 0;
+    dil::PersistTuning ptune;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    dil::PersistJobs gjobs{};
+    dil::PersistTuning gtune;
+    int gmax_iter = -1;
+    void *gws = nullptr;
     std::mutex mu;
 };
 
@@ -127,8 +138,21 @@ int dil_ctx_destroy(dil_ctx *c) {
         cudaDeviceSynchronize();
         if (c->ws) cudaFree(c->ws);
         if (c->stage) cudaFree(c->stage);
+        if (c->pws) cudaFree(c->pws);
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     }
     delete c;
+    return DIL_OK;
+}
+
+int dil_set_tuning(dil_ctx *c, int op, int warps_per_cta, int warps_per_task) {
+    if (!c || op < 0 || op > 2 || warps_per_cta < 1 || warps_per_cta > 8) return DIL_EINVAL;
+    if (warps_per_task != 1 && warps_per_task != 2 && warps_per_task != 4) return DIL_EINVAL;
+    if (warps_per_cta % warps_per_task) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->warps[op] = warps_per_cta;
+    c->wpt[op] = warps_per_task;
     return DIL_OK;
 }
 
@@ -153,7 +177,7 @@ int dil_keygen(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *p
     for (size_t s0 = 0; s0 < n; s0 += chunk) {
         int m = (int)std::min(chunk, n - s0);
         cudaError_t e = dil::launch_keygen(level, m, seeds + 32 * s0, pk + pkb * s0, sk + skb * s0,
-                                           (int32_t *)c->ws, c->warps[0], (cudaStream_t)stream);
+                                           (int32_t *)c->ws, c->warps[0], c->wpt[0], (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -180,7 +204,7 @@ int dil_sign_ex(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_
         cudaError_t e = dil::launch_sign(level, m, sk + skb * s0, msg, msg_off + s0, sig + sigb * s0,
                                          task_status ? task_status + s0 : nullptr,
                                          iterations ? iterations + s0 : nullptr, (int32_t *)c->ws, max_iter,
-                                         c->warps[1], (cudaStream_t)stream);
+                                         c->warps[1], c->wpt[1], (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -207,10 +231,119 @@ int dil_verify(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t
     for (size_t s0 = 0; s0 < n; s0 += chunk) {
         int m = (int)std::min(chunk, n - s0);
         cudaError_t e = dil::launch_verify(level, m, pk + pkb * s0, msg, msg_off + s0, sig + sigb * s0, ok + s0,
-                                           (int32_t *)c->ws, c->warps[2], (cudaStream_t)stream);
+                                           (int32_t *)c->ws, c->warps[2], c->wpt[2], (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
+}
+
+// ---------------------------------------------------------------- persistent
+int dil_set_persistent_tuning(dil_ctx *c, int warps_per_cta, int warps_per_task, int ctas_per_sm, int chunk,
+                              int speculation) {
+    if (!c || warps_per_cta < 1 || warps_per_cta > 8 || ctas_per_sm < 0 || chunk < 1 || speculation < 0)
+        return DIL_EINVAL;
+    if (warps_per_task != 1 && warps_per_task != 2 && warps_per_task != 4) return DIL_EINVAL;
+    if (warps_per_cta % warps_per_task) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->ptune.warps = warps_per_cta;
+    c->ptune.p = warps_per_task;
+    c->ptune.ctas_per_sm = ctas_per_sm;
+    c->ptune.chunk = chunk;
+    c->ptune.spec = speculation;
+    return DIL_OK;
+}
+
+namespace {
+bool same_jobs(const dil::PersistJobs &a, const dil::PersistJobs &b) { return memcmp(&a, &b, sizeof(a)) == 0; }
+bool same_tune(const dil::PersistTuning &a, const dil::PersistTuning &b) {
+    return a.warps == b.warps && a.p == b.p && a.ctas_per_sm == b.ctas_per_sm && a.chunk == b.chunk &&
+           a.spec == b.spec;
+}
+}  // namespace
+
+int dil_sign_persistent(dil_ctx *c, int njobs, const dil_sign_job *jobs, void *stream) {
+    if (!c || njobs < 1 || njobs > dil::PERSIST_MAX_JOBS || !jobs) return DIL_EINVAL;
+    dil::PersistJobs J;
+    memset(&J, 0, sizeof(J));
+    size_t total = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const dil_sign_job &x = jobs[j];
+        if (!level_ok(x.level)) return DIL_EINVAL;
+        if (x.n && (!x.sk || !x.msg_off || !x.sig)) return DIL_EINVAL;
+        J.job[j].level = x.level;
+        J.job[j].n = (int)x.n;
+        J.job[j].start = (int)total;
+        J.job[j].sk = x.sk;
+        J.job[j].msg = x.msg;
+        J.job[j].off = x.msg_off;
+        J.job[j].sig = x.sig;
+        J.job[j].status = x.task_status;
+        J.job[j].iters = x.iterations;
+        total += x.n;
+        if (total > (size_t)INT32_MAX / 2) return DIL_EINVAL;
+    }
+    J.njobs = njobs;
+    J.total = (int)total;
+    if (total == 0) return DIL_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    const size_t need = dil::persist_workspace_bytes(J, c->ptune, c->device);
+    if (need == 0) return DIL_ECUDA;
+    if (need > c->budget) return DIL_ENOMEM;
+    if (need > c->pws_bytes) {
+        if (c->pws) {
+            cudaDeviceSynchronize();
+            cudaFree(c->pws);
+            c->pws = nullptr;
+            c->pws_bytes = 0;
+        }
+        if (cudaMalloc(&c->pws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return DIL_ENOMEM;
+        }
+        c->pws_bytes = need;
+    }
+    const int max_iter = c->max_iter;
+    if (!c->gexec || !same_jobs(J, c->gjobs) || !same_tune(c->ptune, c->gtune) || max_iter != c->gmax_iter ||
+        c->gws != c->pws) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return DIL_ECUDA;
+        // warm the attribute / occupancy queries outside the capture
+        if (dil::persist_workspace_bytes(J, c->ptune, c->device) == 0) return DIL_ECUDA;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return DIL_ECUDA;
+        cudaError_t e = dil::launch_sign_persist(J, c->pws, c->ptune, max_iter, c->device, c->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return DIL_ECUDA;
+        }
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return DIL_ECUDA;
+        }
+        c->gjobs = J;
+        c->gtune = c->ptune;
+        c->gmax_iter = max_iter;
+        c->gws = c->pws;
+    }
+    return cudaGraphLaunch(c->gexec, (cudaStream_t)stream) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
+int dil_persistent_status(dil_ctx *c, void *stream) {
+    if (!c) return DIL_EINVAL;
+    DeviceGuard g(c->device);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DIL_ECUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->pws) return DIL_OK;
+    return dil::persist_error(c->pws);
 }
 
 // ---------------------------------------------------------------- host forms

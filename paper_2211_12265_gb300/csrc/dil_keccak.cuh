@@ -26,7 +26,7 @@ static __constant__ uint64_t c_keccak_rc[24] = {
 
 // FIPS 202 rho rotation offsets, indexed by x + 5y.
 static __constant__ uint8_t c_keccak_rho[25] = {0,  1,  62, 28, 27, 36, 44, 6,  55, 20, 3,  10, 43,
-                                         25, 39, 41, 45, 15, 21, 8,  18, 2,  61, 56, 14};
+                                                25, 39, 41, 45, 15, 21, 8,  18, 2,  61, 56, 14};
 
 // Per-thread shuffle sources and rotation for one warp-level Keccak instance.
 struct KLane {
@@ -85,26 +85,48 @@ __device__ __forceinline__ void keccak_round(uint32_t &lo, uint32_t &hi, const K
     uint32_t a2l = __shfl_sync(FULL, lo, k.b2), a2h = __shfl_sync(FULL, hi, k.b2);
     lo = a0l ^ (~a1l & a2l);
     hi = a0h ^ (~a1h & a2h);
-    // iota
-    if (k.lane0) {
-        lo ^= (uint32_t)rc;
-        hi ^= (uint32_t)(rc >> 32);
-    }
+    // iota (branch-free, so that two interleaved rounds form one basic block)
+    lo ^= k.lane0 ? (uint32_t)rc : 0u;
+    hi ^= k.lane0 ? (uint32_t)(rc >> 32) : 0u;
 }
 
-// One out-of-line copy of the permutation, called by value so the state and
-// the lane parameters stay in registers.
-static __device__ __noinline__ uint2 keccak_f_impl(uint2 s, KLane k) {
+// Out-of-line permutations, called by value so the state stays in registers.
+// The lane parameters are recomputed per call (a few dozen instructions per
+// 24 rounds) instead of occupying registers at every call site.
+static __device__ __noinline__ uint2 keccak_f_impl(uint2 s) {
+    const KLane k = klane_init(threadIdx.x & 31);
     uint32_t lo = s.x, hi = s.y;
 #pragma unroll 4
     for (int r = 0; r < 24; ++r) keccak_round(lo, hi, k, c_keccak_rc[r]);
     return make_uint2(lo, hi);
 }
 
-__device__ __forceinline__ void keccak_f(uint32_t &lo, uint32_t &hi, const KLane &k) {
-    uint2 s = keccak_f_impl(make_uint2(lo, hi), k);
+// Two independent states interleaved round by round: the second instance's
+// shuffles fill the latency of the first's.
+static __device__ __noinline__ uint4 keccak_f2_impl(uint4 s) {
+    const KLane k = klane_init(threadIdx.x & 31);
+    uint32_t lo0 = s.x, hi0 = s.y, lo1 = s.z, hi1 = s.w;
+#pragma unroll 2
+    for (int r = 0; r < 24; ++r) {
+        const uint64_t rc = c_keccak_rc[r];
+        keccak_round(lo0, hi0, k, rc);
+        keccak_round(lo1, hi1, k, rc);
+    }
+    return make_uint4(lo0, hi0, lo1, hi1);
+}
+
+__device__ __forceinline__ void keccak_f(uint32_t &lo, uint32_t &hi) {
+    uint2 s = keccak_f_impl(make_uint2(lo, hi));
     lo = s.x;
     hi = s.y;
+}
+
+__device__ __forceinline__ void keccak_f2(uint32_t &lo0, uint32_t &hi0, uint32_t &lo1, uint32_t &hi1) {
+    uint4 s = keccak_f2_impl(make_uint4(lo0, hi0, lo1, hi1));
+    lo0 = s.x;
+    hi0 = s.y;
+    lo1 = s.z;
+    hi1 = s.w;
 }
 
 // Writes the first `words` 8-byte words of the rate to dst (8-byte aligned).
@@ -123,8 +145,8 @@ __device__ __forceinline__ void pad_word(uint64_t &w, int rem, int rate, int lan
 // Absorbs len bytes from an 8-byte-aligned shared-memory buffer, pads and
 // permutes; afterwards the state holds the first squeeze block.  The buffer
 // must be readable up to the next multiple of 8 beyond len.
-__device__ __forceinline__ void absorb_smem(uint32_t &lo, uint32_t &hi, const KLane &k, const uint8_t *buf,
-                                            int len, int rate, int lane) {
+__device__ __forceinline__ void absorb_smem(uint32_t &lo, uint32_t &hi, const uint8_t *buf, int len, int rate,
+                                            int lane) {
     const int words = rate / 8;
     int off = 0;
     for (; len - off >= rate; off += rate) {
@@ -133,7 +155,7 @@ __device__ __forceinline__ void absorb_smem(uint32_t &lo, uint32_t &hi, const KL
             lo ^= w.x;
             hi ^= w.y;
         }
-        keccak_f(lo, hi, k);
+        keccak_f(lo, hi);
     }
     int rem = len - off;
     if (lane < words) {
@@ -149,15 +171,14 @@ __device__ __forceinline__ void absorb_smem(uint32_t &lo, uint32_t &hi, const KL
         lo ^= (uint32_t)w;
         hi ^= (uint32_t)(w >> 32);
     }
-    keccak_f(lo, hi, k);
+    keccak_f(lo, hi);
 }
 
 // Absorbs the concatenation A || B where A (lenA bytes) is in shared memory and
 // B (lenB bytes, any alignment) is in global memory; pads and permutes.  B is
 // read with coherent loads: it may have been written earlier by the same warp.
-__device__ __forceinline__ void absorb_concat(uint32_t &lo, uint32_t &hi, const KLane &k, const uint8_t *A,
-                                              int lenA, const uint8_t *B, size_t lenB, int rate,
-                                              int lane) {
+__device__ __forceinline__ void absorb_concat(uint32_t &lo, uint32_t &hi, const uint8_t *A, int lenA,
+                                              const uint8_t *B, size_t lenB, int rate, int lane) {
     const int words = rate / 8;
     const size_t total = (size_t)lenA + lenB;
     size_t off = 0;
@@ -178,17 +199,18 @@ __device__ __forceinline__ void absorb_concat(uint32_t &lo, uint32_t &hi, const 
             lo ^= (uint32_t)w;
             hi ^= (uint32_t)(w >> 32);
         }
-        keccak_f(lo, hi, k);
+        keccak_f(lo, hi);
         if (last) break;
         off += rate;
     }
 }
 
-// Absorbs a short seed that fits one block and whose words are given per lane
-// (lanes < nwords provide w), followed by `tail` extra bytes packed in tailw at
-// word index nwords.  Used for fixed-size seeds (rho||nonce, rho'||nonce, c~).
-__device__ __forceinline__ void absorb_seed(uint32_t &lo, uint32_t &hi, const KLane &k, const uint8_t *seed,
-                                            int nwords, uint32_t tailw, int tailbytes, int rate, int lane) {
+// State words of a short padded seed that fits one block: lanes < nwords take
+// 8-byte words of `seed` (8-byte aligned shared memory), lane nwords takes
+// `tailbytes` extra bytes in tailw.  Used for the fixed-size seeds
+// rho || nonce, rho' || nonce and c~; absorb_seed also applies the permutation.
+__device__ __forceinline__ void seed_words(uint32_t &lo, uint32_t &hi, const uint8_t *seed, int nwords,
+                                           uint32_t tailw, int tailbytes, int rate, int lane) {
     uint64_t w = 0;
     if (lane < nwords) {
         uint2 v = *reinterpret_cast<const uint2 *>(seed + 8 * lane);
@@ -199,7 +221,12 @@ __device__ __forceinline__ void absorb_seed(uint32_t &lo, uint32_t &hi, const KL
     if (lane < rate / 8) pad_word(w, 8 * nwords + tailbytes, rate, lane);
     lo = (uint32_t)w;
     hi = (uint32_t)(w >> 32);
-    keccak_f(lo, hi, k);
+}
+
+__device__ __forceinline__ void absorb_seed(uint32_t &lo, uint32_t &hi, const uint8_t *seed, int nwords,
+                                            uint32_t tailw, int tailbytes, int rate, int lane) {
+    seed_words(lo, hi, seed, nwords, tailw, tailbytes, rate, lane);
+    keccak_f(lo, hi);
 }
 
 }  // namespace dil

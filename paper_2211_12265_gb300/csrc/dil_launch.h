@@ -13,15 +13,16 @@ enum Op { OP_KEYGEN = 0, OP_SIGN = 1, OP_VERIFY = 2 };
 // Scratch polynomials (256 int32 each) one task of `op` needs in the plain form.
 size_t scratch_polys(int op, int level);
 // Dynamic shared memory of a CTA with `warps` warps.
-size_t cta_smem_bytes(int warps);
+size_t cta_smem_bytes(int warps, int warps_per_task);
 
+// warps: warps per CTA; p: warps per task (1, 2 or 4; divides warps)
 cudaError_t launch_keygen(int level, int n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk, int32_t *scratch,
-                          int warps, cudaStream_t s);
+                          int warps, int p, cudaStream_t s);
 cudaError_t launch_sign(int level, int n, const uint8_t *sk, const uint8_t *msg, const uint64_t *off,
                         uint8_t *sig, int32_t *status, int32_t *iters, int32_t *scratch, int max_iter,
-                        int warps, cudaStream_t s);
+                        int warps, int p, cudaStream_t s);
 cudaError_t launch_verify(int level, int n, const uint8_t *pk, const uint8_t *msg, const uint64_t *off,
-                          const uint8_t *sig, uint8_t *ok, int32_t *scratch, int warps, cudaStream_t s);
+                          const uint8_t *sig, uint8_t *ok, int32_t *scratch, int warps, int p, cudaStream_t s);
 
 // primitives (test-only entry points)
 cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t *off, uint8_t *out,
@@ -34,6 +35,55 @@ cudaError_t launch_test_expand_mask(int level, int n, const uint8_t *rhop, const
 cudaError_t launch_test_sample_in_ball(int level, int n, const uint8_t *ct, int32_t *out, cudaStream_t s);
 cudaError_t launch_test_rounding(int level, int n, const int32_t *r, const int32_t *z, const uint8_t *h,
                                  int32_t *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- persistent Sign
+// One batch of Sign tasks of one level inside a persistent launch.
+struct PersistJob {
+    int level;
+    int n;
+    int start;   // first global task index of this job
+    const uint8_t *sk;
+    const uint8_t *msg;
+    const uint64_t *off;
+    uint8_t *sig;
+    int32_t *status;
+    int32_t *iters;
+};
+constexpr int PERSIST_MAX_JOBS = 3;
+struct PersistJobs {
+    PersistJob job[PERSIST_MAX_JOBS];
+    int njobs;
+    int total;
+};
+// Per-task scheduling record (device memory, initialised by the task's owner).
+struct PersistTask {
+    int next_r;       // next repetition index to hand out (nonce kappa = l * r)
+    int best_r;       // smallest accepting repetition seen (INT_MAX: none)
+    int committed_r;  // repetition whose signature is in the output
+    int lock;         // commit lock
+    int helpers;      // helper groups reading this task's precomputation
+    int pad[3];
+};
+// Queue header (device memory, zeroed before each launch).
+struct PersistQueue {
+    int next_task;
+    int error;        // DIL_ETIMEOUT when a bounded wait ran out
+    int pad[30];
+};
+struct PersistTuning {
+    int warps = 8;        // warps per CTA
+    int p = 2;            // warps per task group
+    int ctas_per_sm = 0;  // 0 = as many as fit
+    int chunk = 1;        // fresh tasks claimed per queue access
+    int spec = 4;         // helper groups per unfinished task (0 = no speculation)
+};
+// Device bytes a persistent launch needs for `total` tasks of the given levels.
+size_t persist_workspace_bytes(const PersistJobs &J, const PersistTuning &t, int device);
+// Enqueues (memsets + kernel) on s; ws must hold persist_workspace_bytes.
+cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTuning &t, int max_iter_override,
+                                int device, cudaStream_t s);
+// Reads the device error word of the last launch on ws (synchronous).
+int persist_error(void *ws);
 
 // test-only issue-rate probe (thread-ops per SM clock)
 cudaError_t measure_issue_rate(int op, double *rate);

@@ -71,7 +71,7 @@ extern "C" int dil_sign_noalloc(int level, size_t n, const uint8_t *sk, const ui
     const int l = level == 2 ? 4 : level == 3 ? 5 : 7;
     const int max_iter = (65536 - l) / l + 1;   // cap implied by the 16-bit nonce
     cudaError_t e = dil::launch_sign(level, (int)n, sk, msg, msg_off, sig, task_status, nullptr,
-                                     static_cast<int32_t *>(scratch), max_iter, 4, (cudaStream_t)stream);
+                                     static_cast<int32_t *>(scratch), max_iter, 4, 1, (cudaStream_t)stream);
     if (e != cudaSuccess) return DIL_ECUDA;
     return DIL_OK;
 }

@@ -111,17 +111,22 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
 #pragma unroll
         for (int m = 0; m < 4; ++m) ct_bfly(r[m], r[m + 4], z);
     }
-    // level 5 (len 8): pairs (m, m+2), twiddle 16 + 2b + m/4
+    // level 5 (len 8): pairs (m, m+2), twiddles 16 + 2b + {0, 1}
     {
-        const int32_t z0 = zt[16 + 2 * b], z1 = zt[17 + 2 * b];
-        ct_bfly(r[0], r[2], z0);
-        ct_bfly(r[1], r[3], z0);
-        ct_bfly(r[4], r[6], z1);
-        ct_bfly(r[5], r[7], z1);
+        const int2 z = *reinterpret_cast<const int2 *>(zt + 16 + 2 * b);
+        ct_bfly(r[0], r[2], z.x);
+        ct_bfly(r[1], r[3], z.x);
+        ct_bfly(r[4], r[6], z.y);
+        ct_bfly(r[5], r[7], z.y);
     }
-    // level 6 (len 4): pairs (m, m+1), twiddle 32 + 4b + m/2
-#pragma unroll
-    for (int m = 0; m < 8; m += 2) ct_bfly(r[m], r[m + 1], zt[32 + 4 * b + m / 2]);
+    // level 6 (len 4): pairs (m, m+1), twiddles 32 + 4b + {0..3}
+    {
+        const int4 z = *reinterpret_cast<const int4 *>(zt + 32 + 4 * b);
+        ct_bfly(r[0], r[1], z.x);
+        ct_bfly(r[2], r[3], z.y);
+        ct_bfly(r[4], r[5], z.z);
+        ct_bfly(r[6], r[7], z.w);
+    }
     // exchange L1 -> L2
 #pragma unroll
     for (int m = 0; m < 8; ++m) buf[base1 + 4 * m + (m >> 1)] = r[m];
@@ -129,33 +134,44 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
 #pragma unroll
     for (int m = 0; m < 8; ++m) r[m] = buf[9 * lane + m];
     __syncwarp();
-    // level 7 (len 2): pairs (m, m+2), twiddle 64 + 2t + m/4
+    // level 7 (len 2): pairs (m, m+2), twiddles 64 + 2t + {0, 1} (one 8-byte
+    // load per lane: a half-warp reads 128 contiguous bytes, conflict-free)
     {
-        const int32_t z0 = zt[64 + 2 * lane], z1 = zt[65 + 2 * lane];
-        ct_bfly(r[0], r[2], z0);
-        ct_bfly(r[1], r[3], z0);
-        ct_bfly(r[4], r[6], z1);
-        ct_bfly(r[5], r[7], z1);
+        const int2 z = *reinterpret_cast<const int2 *>(zt + 64 + 2 * lane);
+        ct_bfly(r[0], r[2], z.x);
+        ct_bfly(r[1], r[3], z.x);
+        ct_bfly(r[4], r[6], z.y);
+        ct_bfly(r[5], r[7], z.y);
     }
-    // level 8 (len 1): pairs (m, m+1), twiddle 128 + 4t + m/2
-#pragma unroll
-    for (int m = 0; m < 8; m += 2) ct_bfly(r[m], r[m + 1], zt[128 + 4 * lane + m / 2]);
+    // level 8 (len 1): pairs (m, m+1), twiddles 128 + 4t + {0..3} (16-byte load)
+    {
+        const int4 z = *reinterpret_cast<const int4 *>(zt + 128 + 4 * lane);
+        ct_bfly(r[0], r[1], z.x);
+        ct_bfly(r[2], r[3], z.y);
+        ct_bfly(r[4], r[5], z.z);
+        ct_bfly(r[6], r[7], z.w);
+    }
 }
 
 // Inverse NTT.  In: L2, |r| < q.  Out: L0, |r| < q, equal to INTT(in) * 2^32,
 // so it turns pointwise Montgomery products into plain coefficients.
 // izt: the inverse twiddles in shared memory.
 __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_t *izt, int lane) {
-    // len 1: pairs (m, m+1), twiddle 128 + 4t + m/2
-#pragma unroll
-    for (int m = 0; m < 8; m += 2) gs_bfly(r[m], r[m + 1], izt[128 + 4 * lane + m / 2]);
-    // len 2: pairs (m, m+2), twiddle 64 + 2t + m/4
+    // len 1: pairs (m, m+1), twiddles 128 + 4t + {0..3}
     {
-        const int32_t z0 = izt[64 + 2 * lane], z1 = izt[65 + 2 * lane];
-        gs_bfly(r[0], r[2], z0);
-        gs_bfly(r[1], r[3], z0);
-        gs_bfly(r[4], r[6], z1);
-        gs_bfly(r[5], r[7], z1);
+        const int4 z = *reinterpret_cast<const int4 *>(izt + 128 + 4 * lane);
+        gs_bfly(r[0], r[1], z.x);
+        gs_bfly(r[2], r[3], z.y);
+        gs_bfly(r[4], r[5], z.z);
+        gs_bfly(r[6], r[7], z.w);
+    }
+    // len 2: pairs (m, m+2), twiddles 64 + 2t + {0, 1}
+    {
+        const int2 z = *reinterpret_cast<const int2 *>(izt + 64 + 2 * lane);
+        gs_bfly(r[0], r[2], z.x);
+        gs_bfly(r[1], r[3], z.x);
+        gs_bfly(r[4], r[6], z.y);
+        gs_bfly(r[5], r[7], z.y);
     }
     // exchange L2 -> L1
 #pragma unroll
@@ -165,16 +181,21 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
 #pragma unroll
     for (int m = 0; m < 8; ++m) r[m] = buf[base1 + 4 * m + (m >> 1)];
     __syncwarp();
-    // len 4: pairs (m, m+1), twiddle 32 + 4b + m/2
-#pragma unroll
-    for (int m = 0; m < 8; m += 2) gs_bfly(r[m], r[m + 1], izt[32 + 4 * b + m / 2]);
-    // len 8: pairs (m, m+2), twiddle 16 + 2b + m/4
+    // len 4: pairs (m, m+1), twiddles 32 + 4b + {0..3}
     {
-        const int32_t z0 = izt[16 + 2 * b], z1 = izt[17 + 2 * b];
-        gs_bfly(r[0], r[2], z0);
-        gs_bfly(r[1], r[3], z0);
-        gs_bfly(r[4], r[6], z1);
-        gs_bfly(r[5], r[7], z1);
+        const int4 z = *reinterpret_cast<const int4 *>(izt + 32 + 4 * b);
+        gs_bfly(r[0], r[1], z.x);
+        gs_bfly(r[2], r[3], z.y);
+        gs_bfly(r[4], r[5], z.z);
+        gs_bfly(r[6], r[7], z.w);
+    }
+    // len 8: pairs (m, m+2), twiddles 16 + 2b + {0, 1}
+    {
+        const int2 z = *reinterpret_cast<const int2 *>(izt + 16 + 2 * b);
+        gs_bfly(r[0], r[2], z.x);
+        gs_bfly(r[1], r[3], z.x);
+        gs_bfly(r[4], r[6], z.y);
+        gs_bfly(r[5], r[7], z.y);
     }
     // len 16: pairs (m, m+4), twiddle 8 + b
     {

@@ -1,0 +1,385 @@
+// Persistent Sign with a device work queue (section 4.3 of arXiv 2211.12265,
+// dynamic task scheduling, redesigned to run entirely on the device).
+//
+// Workers are groups of P warps that stay resident for the whole launch.  A
+// worker takes a fresh task from the queue (atomic cursor), prepares it into
+// its own scratch slot (mu, rho', A^, s^1, s^2, t^0), publishes the slot, and
+// then draws repetition indices r from the task's counter, running the loop
+// body with nonce kappa = l r.  When the queue is empty, idle workers become
+// helpers: they join an unfinished task (at most `spec` per task), read its
+// published precomputation through L2 and draw further r from the same
+// counter, i.e. they evaluate predicted nonces.  Every accepting r lowers the
+// task's best_r; the signature in the output is written under a per-task lock
+// only by a smaller r than the one already committed, so the result is the
+// signature of the smallest accepting nonce: exactly the sequential result.
+// All r below the final one are evaluated (they are handed out in order and an
+// r is skipped only when it exceeds an accepted one).
+//
+// Waits (commit lock, an owner waiting for its helpers before reusing its
+// slot) spin at most PERSIST_SPIN_LIMIT times; then the kernel records
+// DIL_ETIMEOUT in the queue's error word and continues.  The holders of these
+// waits never wait on anything themselves, so the limit is a safety net only.
+#include <climits>
+
+#include "../../include/dil.h"
+#include "dil_kern.cuh"
+
+namespace dil {
+
+constexpr int PERSIST_SPIN_LIMIT = 1 << 22;
+constexpr int PERSIST_META_POLYS = 1;   // mu (64 B) and rho' (64 B) of a slot's task
+
+__device__ __forceinline__ int ld_l2(const int *p) { return __ldcg(p); }
+
+__device__ __forceinline__ const PersistJob &job_of(const PersistJobs &J, int t, int &local) {
+    int j = 0;
+    while (j + 1 < J.njobs && t >= J.job[j + 1].start) ++j;
+    local = t - J.job[j].start;
+    return J.job[j];
+}
+
+template <int LEVEL>
+__device__ __forceinline__ int iter_cap(int override_cap) {
+    return (override_cap > 0 && override_cap < Lv<LEVEL>::MAX_ITER) ? override_cap : Lv<LEVEL>::MAX_ITER;
+}
+
+struct PersistCtx {
+    PersistQueue *q;
+    PersistTask *tasks;
+    int *slot_task;
+    int32_t *scratch;
+    int slot_polys;
+    int slots;
+    int max_iter_override;
+    int spec;
+};
+
+// Writes the signature of repetition r for task t if r beats the committed one.
+template <int LEVEL, int P>
+__device__ void commit(const PersistCtx &pc, PersistTask &tk, int r, const PersistJob &jb, int local,
+                       const int32_t *itr, GroupSmem &gs, int g, int bar, int lane) {
+    const bool leader = g == 0 && lane == 0;
+    if (leader) {
+        atomicMin(&tk.best_r, r);
+        int acquired = 0;
+        for (int i = 0; i < PERSIST_SPIN_LIMIT; ++i) {
+            if (atomicCAS(&tk.lock, 0, 1) == 0) {
+                acquired = 1;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!acquired) atomicExch(&pc.q->error, DIL_ETIMEOUT);
+        __threadfence();
+        const int win = acquired && r < atomicOr(&tk.committed_r, 0);
+        gs.claim2 = acquired ? (win ? 2 : 1) : 0;
+    }
+    group_sync<P>(bar);
+    const int st = *(volatile int *)&gs.claim2;
+    if (st == 2) {
+        sign_pack<LEVEL, P>(jb.sig + (size_t)local * Lv<LEVEL>::SIG, itr, gs, g, lane);
+        if (leader) {
+            if (jb.status) jb.status[local] = 0;
+            if (jb.iters) jb.iters[local] = r + 1;
+        }
+    }
+    __threadfence();
+    group_sync<P>(bar);
+    if (leader && st >= 1) {
+        if (st == 2) atomicExch(&tk.committed_r, r);
+        __threadfence();
+        atomicExch(&tk.lock, 0);
+    }
+    group_sync<P>(bar);
+}
+
+// Draws repetitions of task t until one accepts, the counter passes an
+// accepted r, or the cap is reached.  pre: the task's precomputation.
+template <int LEVEL, int P>
+__device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const PersistJob &jb, int local,
+                                const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws, const int32_t *zt,
+                                const int32_t *izt, int g, int bar, int lane) {
+    const int cap = iter_cap<LEVEL>(pc.max_iter_override);
+    const bool leader = g == 0 && lane == 0;
+    for (;;) {
+        if (leader) {
+            const int r = atomicAdd(&tk.next_r, 1);
+            const int best = atomicOr(&tk.best_r, 0);
+            gs.claim2 = (r < cap && r < best) ? r : -1;
+        }
+        group_sync<P>(bar);
+        const int r = *(volatile int *)&gs.claim2;
+        group_sync<P>(bar);
+        if (r < 0) break;
+        if (sign_attempt<LEVEL, P>(Lv<LEVEL>::L * r, pre, itr, gs, ws, zt, izt, g, bar, lane)) {
+            commit<LEVEL, P>(pc, tk, r, jb, local, itr, gs, g, bar, lane);
+            break;
+        }
+    }
+}
+
+// Owns task t: prepare, publish, repeat, release, and report a capped task.
+template <int LEVEL, int P>
+__device__ void own_task(const PersistCtx &pc, int t, const PersistJob &jb, int local, int slot, int32_t *mine,
+                         GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar,
+                         int lane) {
+    using V = Lv<LEVEL>;
+    using S = Scratch<LEVEL>;
+    const bool leader = g == 0 && lane == 0;
+    PersistTask &tk = pc.tasks[t];
+    if (leader) {
+        tk.next_r = 0;
+        tk.best_r = INT_MAX;
+        tk.committed_r = INT_MAX;
+        tk.lock = 0;
+        tk.helpers = 0;
+    }
+    const uint64_t m0 = jb.off[local], m1 = jb.off[local + 1];
+    sign_prepare<LEVEL, P>(jb.sk + (size_t)local * V::SK, jb.msg + m0, (size_t)(m1 - m0), mine, gs, ws, zt, g, bar,
+                           lane);
+    uint8_t *meta = reinterpret_cast<uint8_t *>(mine + S::SIGN_POLYS * N);
+    if (g == 0) {
+        meta[lane] = gs.hb[HB_MU + lane];
+        meta[32 + lane] = gs.hb[HB_MU + 32 + lane];
+        meta[64 + lane] = gs.rhop[lane];
+        meta[96 + lane] = gs.rhop[32 + lane];
+    }
+    __threadfence();
+    group_sync<P>(bar);
+    if (leader) atomicExch(&pc.slot_task[slot], t);
+    int32_t *itr = mine + S::PRE_POLYS * N;
+    run_repetitions<LEVEL, P>(pc, tk, jb, local, mine, itr, gs, ws, zt, izt, g, bar, lane);
+    if (leader) {
+        atomicExch(&pc.slot_task[slot], -1);
+        __threadfence();
+        int waited = 0;
+        while (atomicAdd(&tk.helpers, 0) != 0) {
+            if (++waited > PERSIST_SPIN_LIMIT) {
+                atomicExch(&pc.q->error, DIL_ETIMEOUT);
+                break;
+            }
+            __nanosleep(128);
+        }
+        gs.claim2 = (atomicOr(&tk.best_r, 0) == INT_MAX) ? 1 : 0;
+    }
+    group_sync<P>(bar);
+    const int capped = *(volatile int *)&gs.claim2;
+    group_sync<P>(bar);
+    if (capped) {
+        sign_zero<LEVEL, P>(jb.sig + (size_t)local * V::SIG, g, lane);
+        if (leader) {
+            if (jb.status) jb.status[local] = DIL_EITER;
+            if (jb.iters) jb.iters[local] = iter_cap<LEVEL>(pc.max_iter_override);
+        }
+    }
+}
+
+// Helps task t owned by slot s (the caller has registered as a helper).
+template <int LEVEL, int P>
+__device__ void help_task(const PersistCtx &pc, int t, const PersistJob &jb, int local, int s, int32_t *mine,
+                          GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar,
+                          int lane) {
+    using S = Scratch<LEVEL>;
+    const int32_t *owner = pc.scratch + (size_t)s * pc.slot_polys * N;
+    const uint8_t *meta = reinterpret_cast<const uint8_t *>(owner + S::SIGN_POLYS * N);
+    if (g == 0) {
+        gs.hb[HB_MU + lane] = __ldcg(meta + lane);
+        gs.hb[HB_MU + 32 + lane] = __ldcg(meta + 32 + lane);
+        gs.rhop[lane] = __ldcg(meta + 64 + lane);
+        gs.rhop[32 + lane] = __ldcg(meta + 96 + lane);
+    }
+    group_sync<P>(bar);
+    run_repetitions<LEVEL, P>(pc, pc.tasks[t], jb, local, owner, mine + S::PRE_POLYS * N, gs, ws, zt, izt, g, bar,
+                              lane);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQueue *q, PersistTask *tasks,
+                                                         int *slot_task, int32_t *scratch, int slot_polys,
+                                                         int max_iter_override, int chunk, int spec) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const CtaView v = cta_setup<P>(smem);
+    GroupSmem &gs = *v.gs;
+    WarpSmem &ws = *v.ws;
+    const int g = v.g, bar = v.bar, lane = v.lane;
+    const bool leader = g == 0 && lane == 0;
+    PersistCtx pc{q, tasks, slot_task, scratch, slot_polys, (int)gridDim.x * v.groups, max_iter_override, spec};
+    const int slot = blockIdx.x * v.groups + v.group;
+    int32_t *mine = scratch + (size_t)slot * slot_polys * N;
+    // fresh tasks
+    for (;;) {
+        if (leader) gs.claim = atomicAdd(&q->next_task, chunk);
+        group_sync<P>(bar);
+        const int c0 = *(volatile int *)&gs.claim;
+        group_sync<P>(bar);
+        if (c0 >= J.total) break;
+        const int c1 = min(c0 + chunk, J.total);
+        for (int t = c0; t < c1; ++t) {
+            int local;
+            const PersistJob &jb = job_of(J, t, local);
+            switch (jb.level) {
+                case 2: own_task<2, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+                case 3: own_task<3, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+                default: own_task<5, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+            }
+        }
+    }
+    if (spec <= 0) return;
+    // speculative help on unfinished tasks (predicted nonces)
+    int start = (int)(((unsigned)slot * 2654435761u) % (unsigned)pc.slots);
+    for (int round = 0; round < 4096; ++round) {
+        if (g == 0) {
+            int found_s = -1, found_t = -1;
+            for (int base = 0; base < pc.slots && found_s < 0; base += 32) {
+                const int idx = base + lane;
+                const int s = (start + idx) % pc.slots;
+                int t = idx < pc.slots ? ld_l2(slot_task + s) : -1;
+                bool cand = false;
+                if (t >= 0) cand = ld_l2(&tasks[t].best_r) == INT_MAX && ld_l2(&tasks[t].helpers) < spec;
+                const unsigned m = __ballot_sync(FULL, cand);
+                if (m) {
+                    const int src = __ffs(m) - 1;
+                    found_s = __shfl_sync(FULL, s, src);
+                    found_t = __shfl_sync(FULL, t, src);
+                }
+            }
+            int joined = 0;
+            if (found_s >= 0 && lane == 0) {
+                atomicAdd(&tasks[found_t].helpers, 1);
+                __threadfence();
+                if (atomicOr(&slot_task[found_s], 0) == found_t && atomicOr(&tasks[found_t].best_r, 0) == INT_MAX)
+                    joined = 1;
+                else
+                    atomicSub(&tasks[found_t].helpers, 1);
+            }
+            joined = __shfl_sync(FULL, joined, 0);
+            if (lane == 0) {
+                gs.claim = found_s < 0 ? -2 : (joined ? found_s : -1);
+                gs.claim2 = found_t;
+            }
+        }
+        group_sync<P>(bar);
+        const int s = *(volatile int *)&gs.claim, t = *(volatile int *)&gs.claim2;
+        group_sync<P>(bar);
+        if (s == -2) break;
+        if (s == -1) continue;
+        int local;
+        const PersistJob &jb = job_of(J, t, local);
+        switch (jb.level) {
+            case 2: help_task<2, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+            case 3: help_task<3, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+            default: help_task<5, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+        }
+        __threadfence();
+        group_sync<P>(bar);
+        if (leader) atomicSub(&tasks[t].helpers, 1);
+        start = (start + 1) % pc.slots;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int slot_polys_for(const PersistJobs &J) {
+    int m = 0;
+    for (int j = 0; j < J.njobs; ++j) {
+        int p = (int)scratch_polys(OP_SIGN, J.job[j].level);
+        m = p > m ? p : m;
+    }
+    return m + PERSIST_META_POLYS;
+}
+
+template <int P>
+cudaError_t grid_for(const PersistTuning &t, int device, int &grid) {
+    int sms = 0, occ = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    const size_t smem = cta_bytes(t.warps, P);
+    e = cudaFuncSetAttribute(k_sign_persist<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sign_persist<P>, t.warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int per_sm = (t.ctas_per_sm > 0 && t.ctas_per_sm < occ) ? t.ctas_per_sm : occ;
+    grid = sms * per_sm;
+    return cudaSuccess;
+}
+
+cudaError_t grid_of(const PersistTuning &t, int device, int &grid) {
+    switch (t.p) {
+        case 1: return grid_for<1>(t, device, grid);
+        case 2: return grid_for<2>(t, device, grid);
+        case 4: return grid_for<4>(t, device, grid);
+    }
+    return cudaErrorInvalidValue;
+}
+
+struct Layout {
+    size_t q, tasks, slots, scratch, total;
+    int nslots, slot_polys, grid;
+};
+
+cudaError_t layout_of(const PersistJobs &J, const PersistTuning &t, int device, Layout &L) {
+    cudaError_t e = grid_of(t, device, L.grid);
+    if (e != cudaSuccess) return e;
+    L.nslots = L.grid * (t.warps / t.p);
+    L.slot_polys = slot_polys_for(J);
+    L.q = 0;
+    L.tasks = al256(sizeof(PersistQueue));
+    L.slots = L.tasks + al256((size_t)J.total * sizeof(PersistTask));
+    L.scratch = L.slots + al256((size_t)L.nslots * sizeof(int));
+    L.total = L.scratch + (size_t)L.nslots * L.slot_polys * N * sizeof(int32_t);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t persist_workspace_bytes(const PersistJobs &J, const PersistTuning &t, int device) {
+    Layout L;
+    if (layout_of(J, t, device, L) != cudaSuccess) return 0;
+    return L.total;
+}
+
+cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTuning &t, int max_iter_override,
+                                int device, cudaStream_t s) {
+    if (J.total <= 0) return cudaSuccess;
+    Layout L;
+    cudaError_t e = layout_of(J, t, device, L);
+    if (e != cudaSuccess) return e;
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    e = cudaMemsetAsync(base + L.q, 0, sizeof(PersistQueue), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(base + L.slots, 0xFF, (size_t)L.nslots * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    auto *q = reinterpret_cast<PersistQueue *>(base + L.q);
+    auto *tasks = reinterpret_cast<PersistTask *>(base + L.tasks);
+    auto *slot_task = reinterpret_cast<int *>(base + L.slots);
+    auto *scratch = reinterpret_cast<int32_t *>(base + L.scratch);
+    const size_t smem = cta_bytes(t.warps, t.p);
+    const int chunk = t.chunk > 0 ? t.chunk : 1;
+    switch (t.p) {
+        case 1:
+            k_sign_persist<1><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
+                                                                 max_iter_override, chunk, t.spec);
+            break;
+        case 2:
+            k_sign_persist<2><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
+                                                                 max_iter_override, chunk, t.spec);
+            break;
+        default:
+            k_sign_persist<4><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
+                                                                 max_iter_override, chunk, t.spec);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+int persist_error(void *ws) {
+    PersistQueue h;
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DIL_ECUDA;
+    return h.error ? DIL_ETIMEOUT : DIL_OK;
+}
+
+}  // namespace dil

@@ -1,34 +1,30 @@
 // Kernels behind the test-only entry points: one primitive of the hot path per
 // kernel (SHAKE, NTT/INTT, the four samplers, the coefficient functions), each
 // built from the same device functions the fused procedure kernels use.
-#include "dil_launch.h"
-#include "dil_procs.cuh"
+#include "dil_kern.cuh"
 
 namespace dil {
 
 #define PRIM_PROLOGUE                                                             \
     extern __shared__ __align__(16) uint8_t smem[];                               \
-    int32_t *zt = reinterpret_cast<int32_t *>(smem);                              \
-    int32_t *izt = zt + 256;                                                      \
-    WarpSmem *wsa = reinterpret_cast<WarpSmem *>(smem + CTA_TABLE_BYTES);         \
-    load_zetas(zt, izt);                                                          \
-    __syncthreads();                                                              \
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;                   \
-    const int item = blockIdx.x * (blockDim.x >> 5) + warp;                       \
+    const CtaView v = cta_setup<1>(smem);                                         \
+    const int item = blockIdx.x * v.groups + v.group;                             \
     if (item >= n) return;                                                        \
-    WarpSmem &ws = wsa[warp];                                                     \
-    const KLane k = klane_init(lane);                                             \
-    (void)zt; (void)izt; (void)ws; (void)k;
+    const int lane = v.lane;                                                      \
+    const int32_t *zt = v.zt, *izt = v.izt;                                       \
+    GroupSmem &gs = *v.gs;                                                        \
+    WarpSmem &ws = *v.ws;                                                         \
+    (void)zt; (void)izt; (void)gs; (void)ws;
 
 constexpr int PRIM_WARPS = 4;
 
 __global__ void k_test_shake(int n, int rate, const uint8_t *in, const uint64_t *off, uint8_t *out, int outlen) {
     PRIM_PROLOGUE
     uint32_t lo = 0, hi = 0;
-    absorb_concat(lo, hi, k, ws.sq, 0, in + off[item], (size_t)(off[item + 1] - off[item]), rate, lane);
+    absorb_concat(lo, hi, ws.sq, 0, in + off[item], (size_t)(off[item + 1] - off[item]), rate, lane);
     uint8_t *o = out + (size_t)item * outlen;
     for (int p = 0; p < outlen; p += rate) {
-        if (p) keccak_f(lo, hi, k);
+        if (p) keccak_f(lo, hi);
         squeeze_words(lo, hi, ws.sq, rate / 8, lane);
         __syncwarp();
         for (int b = lane; b < rate && p + b < outlen; b += 32) o[p + b] = ws.sq[b];
@@ -64,11 +60,11 @@ template <int LEVEL>
 __global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
-    stage_bytes(ws.rho, rho + (size_t)item * 32, 32, lane);
+    stage_bytes(gs.rho, rho + (size_t)item * 32, 32, lane);
     __syncwarp();
     for (int i = 0; i < V::K; ++i)
         for (int j = 0; j < V::L; ++j) {
-            expand_a_poly(ws.rho, i, j, ws.buf, ws.sq, k, lane);
+            expand_a_poly(gs.rho, i, j, ws.buf, ws.sq, lane);
             int32_t a[8];
             read_buf_l2(a, ws.buf, lane);
             __syncwarp();
@@ -80,10 +76,10 @@ template <int LEVEL>
 __global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
-    stage_bytes(ws.rhop, rhop + (size_t)item * 64, 64, lane);
+    stage_bytes(gs.rhop, rhop + (size_t)item * 64, 64, lane);
     __syncwarp();
     for (int j = 0; j < V::L + V::K; ++j) {
-        expand_s_poly<V::ETA>(ws.rhop, j, ws.buf, ws.sq, k, lane);
+        expand_s_poly<V::ETA>(gs.rhop, j, ws.buf, ws.sq, lane);
         int32_t a[8];
         read_buf_l0(a, ws.buf, lane);
         __syncwarp();
@@ -95,11 +91,11 @@ template <int LEVEL>
 __global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
-    stage_bytes(ws.rhop, rhop + (size_t)item * 64, 64, lane);
+    stage_bytes(gs.rhop, rhop + (size_t)item * 64, 64, lane);
     __syncwarp();
     for (int j = 0; j < V::L; ++j) {
         int32_t a[8];
-        expand_mask_poly<V::ZBITS, V::GAMMA1>(ws.rhop, kappa[item] + j, a, ws.sq, k, lane);
+        expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + j, a, ws.sq, lane);
         store_l0(out + ((size_t)item * V::L + j) * N, a, lane);
     }
 }
@@ -108,9 +104,9 @@ template <int LEVEL>
 __global__ void k_test_sample_in_ball(int n, const uint8_t *ct, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
-    stage_bytes(ws.ctilde, ct + (size_t)item * 32, 32, lane);
+    stage_bytes(gs.ctilde, ct + (size_t)item * 32, 32, lane);
     __syncwarp();
-    sample_in_ball<V::TAU>(ws.ctilde, ws.buf, ws.sq, k, lane);
+    sample_in_ball<V::TAU>(gs.ctilde, ws.buf, ws.sq, lane);
     int32_t a[8];
     read_buf_l0(a, ws.buf, lane);
     store_l0(out + (size_t)item * N, a, lane);
@@ -135,7 +131,7 @@ __global__ void k_test_rounding(int n, const int32_t *r, const int32_t *z, const
 template <class Kern, class... Args>
 static cudaError_t launch_prim(Kern kern, int n, cudaStream_t s, Args... args) {
     if (n <= 0) return cudaSuccess;
-    size_t smem = cta_smem_bytes(PRIM_WARPS);
+    size_t smem = cta_bytes(PRIM_WARPS, 1);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(n + PRIM_WARPS - 1) / PRIM_WARPS, PRIM_WARPS * 32, smem, s>>>(n, args...);

@@ -1,35 +1,76 @@
-// Fused warp-per-task procedure bodies: Alg 1 (Gen), Alg 2 (Sign) and Alg 3
-// (Verify) of arXiv 2211.12265.  One warp owns one task end to end (the
-// paper's single-warp form, section 4.2), keeping polynomials in registers and
-// a small per-warp shared-memory area, and spilling the per-task vectors that
-// do not fit (A^, s^1, s^2, t^0, y, y^, w, z) to a global scratch area.
+// Fused procedure bodies: Alg 1 (Gen), Alg 2 (Sign) and Alg 3 (Verify) of
+// arXiv 2211.12265, run by a group of P warps per task (P = 1 is the paper's
+// single-warp form; P = 2 or 4 spreads a task's polynomials over several warps
+// like its four-warp form, section 3.1, cutting per-task latency).
 //
-// Global scratch polynomials hold 256 int32 each.  NTT-domain polynomials are
-// stored in index order (lane t reads 8t..8t+7 with two 16-byte loads); plain
-// polynomials in coefficient order (lane t reads t + 32m, coalesced).
+// Work inside a task is cut into polynomials (or pairs of polynomials whose
+// sponges run interleaved); warp g of the group takes every P-th unit.  The
+// group synchronises with a named barrier between phases.  Hashes over the
+// whole task (mu, rho', c~, tr) run on one warp.  Per-warp shared memory holds
+// NTT exchange buffers and squeezed blocks; per-group shared memory holds the
+// task's seeds, the packed w1 hash input, c~ and the hint masks.  Per-task
+// vectors that do not fit on chip (A^, s^1, s^2, t^0, y, y^, w, z) live in a
+// global scratch area: NTT-domain polynomials in index order (lane t reads
+// 8t..8t+7 with two 16-byte loads), plain ones in coefficient order (lane t
+// reads t + 32m, coalesced).
 #pragma once
 #include "dil_sample.cuh"
 
 namespace dil {
 
-// Per-warp shared memory.  Every region is 8-byte aligned.
+// Per-warp shared memory.
 struct __align__(16) WarpSmem {
-    int32_t buf[288];       // NTT exchanges / sampled polynomials (padded)
-    uint8_t sq[688];        // squeezed SHAKE blocks (5 x 136 + slack)
-    uint8_t hb[1128];       // K (32) | mu (64) | packed w1 (k * POLYW1) | slack
-    uint8_t rhop[64];       // rho'
+    int32_t buf[288];    // NTT exchanges / sampled polynomial (padded)
+    int32_t buf2[288];   // second sampled polynomial of a pair
+    uint8_t sq[688];     // squeezed SHAKE blocks (5 x 136 + slack)
+    uint8_t sq2[688];    // squeezed blocks of the second sponge of a pair
+};
+
+// Per-task (per-group) shared memory.  Every region is 8-byte aligned.
+struct __align__(16) GroupSmem {
+    uint8_t hb[1128];    // K (32) | mu (64) | packed w1 (k * POLYW1) | slack
+    uint8_t rhop[64];
     uint8_t rho[32];
     uint8_t ctilde[32];
     uint8_t tr[32];
-    uint32_t hmask[64];     // hint bits: 8 words per polynomial
+    uint32_t hmask[64];  // hint bits: 8 words per polynomial
+    int flag;            // reject flag of the current attempt
+    int count;           // hint count of the current attempt
+    int claim;           // broadcast slots of the persistent scheduler
+    int claim2;
 };
 
 constexpr int HB_K = 0, HB_MU = 32, HB_W1 = 96;
 constexpr int CTA_TABLE_BYTES = 2 * 256 * 4;
 
+// Synchronises the P warps of one task group (barrier id `bar`).
+template <int P>
+__device__ __forceinline__ void group_sync(int bar) {
+    if constexpr (P == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * P) : "memory");
+    }
+}
+
+// Units of work: polynomials [0, M) cut into pairs when every warp of the
+// group gets at least one pair, else into single polynomials.
+template <int M, int P>
+struct Units {
+    static constexpr int SIZE = (M >= 2 * P) ? 2 : 1;
+};
+
 __device__ __forceinline__ void load_l2(int32_t v[8], const int32_t *__restrict__ p, int lane) {
     const int4 *q = reinterpret_cast<const int4 *>(p + 8 * lane);
     int4 a = q[0], b = q[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// As load_l2, through L2 only (data written by warps on other SMs).
+__device__ __forceinline__ void load_l2_cg(int32_t v[8], const int32_t *p, int lane) {
+    const int4 *q = reinterpret_cast<const int4 *>(p + 8 * lane);
+    int4 a = __ldcg(q), b = __ldcg(q + 1);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
@@ -72,7 +113,7 @@ __device__ __forceinline__ void unpack_poly_l0(int32_t v[8], const uint8_t *__re
     __syncwarp();
 }
 
-// Writes 8 consecutive coefficients (lane t: 8t..8t+7) as `off - v` in BITS bits.
+// Writes 8 consecutive coefficients (lane t: 8t..8t+7) as `off + sign v` in BITS bits.
 template <int BITS>
 __device__ __forceinline__ void pack_seq(uint8_t *dst_poly, const int32_t v[8], int32_t off, int sign, int lane) {
     uint32_t u[8];
@@ -81,76 +122,120 @@ __device__ __forceinline__ void pack_seq(uint8_t *dst_poly, const int32_t v[8], 
     pack8<BITS>(dst_poly + BITS * lane, u);
 }
 
-// Per-task scratch layout (in polynomials of 256 int32).
+// Per-task scratch layout (in polynomials of 256 int32).  Sign's area is a
+// precomputation part (A^, s^1, s^2, t^0: read-only once prepared, shareable
+// between workers) followed by a per-repetition part (y, y^, w, z: private to
+// the worker running a repetition).
 template <int LEVEL> struct Scratch {
     using V = Lv<LEVEL>;
     static constexpr int AH = 0;
     static constexpr int S1H = AH + V::K * V::L;
     static constexpr int S2H = S1H + V::L;
     static constexpr int T0H = S2H + V::K;
-    static constexpr int Y = T0H + V::K;
+    static constexpr int PRE_POLYS = T0H + V::K;
+    // offsets inside the per-repetition part
+    static constexpr int Y = 0;
     static constexpr int YH = Y + V::L;
     static constexpr int W = YH + V::L;
     static constexpr int Z = W + V::K;
-    static constexpr int SIGN_POLYS = Z + V::L;
+    static constexpr int ITR_POLYS = Z + V::L;
+    static constexpr int SIGN_POLYS = PRE_POLYS + ITR_POLYS;
     static constexpr int GEN_POLYS = V::L;     // s^1
     static constexpr int VERIFY_POLYS = V::L;  // z^
 };
 
+// acc = sum_j A^_ij o v^_j (pointwise Montgomery products) for one row i of A^,
+// sampling A^ on the fly two polynomials at a time; v^_j (layout L2) are the
+// l polynomials at `vhat`.  acc is overwritten.
+__device__ __forceinline__ void accumulate_a_row(int32_t acc[8], const uint8_t *rho, int i, int l,
+                                                 const int32_t *vhat, WarpSmem &ws, int lane) {
+    int32_t a[8], v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0;
+    for (int j = 0; j < l; j += 2) {
+        const bool two = j + 1 < l;
+        if (two)
+            expand_a_pair(rho, i, j, i, j + 1, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
+        else
+            expand_a_poly(rho, i, j, ws.buf, ws.sq, lane);
+        read_buf_l2(a, ws.buf, lane);
+        load_l2(v, vhat + j * N, lane);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], v[m]);
+        if (two) {
+            read_buf_l2(a, ws.buf2, lane);
+            load_l2(v, vhat + (j + 1) * N, lane);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], v[m]);
+        }
+        __syncwarp();
+    }
+}
+
+// c^ = NTT(SampleInBall(c~)) in layout L2 (every warp of a group computes it).
+template <int LEVEL>
+__device__ __forceinline__ void challenge_hat(int32_t ch[8], const uint8_t *ctilde, WarpSmem &ws,
+                                              const int32_t *zt, int lane) {
+    sample_in_ball<Lv<LEVEL>::TAU>(ctilde, ws.buf, ws.sq, lane);
+    read_buf_l0(ch, ws.buf, lane);
+    __syncwarp();
+    ntt_fwd(ch, ws.buf, zt, lane);
+}
+
 // -------------------------------------------------------------------------
 // Alg 1: Gen.  seed: 32 bytes.  pk, sk: outputs.  scratch: GEN_POLYS polys.
 // -------------------------------------------------------------------------
-template <int LEVEL>
-__device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t *sk,
-                         int32_t *__restrict__ scratch, WarpSmem &ws, const int32_t *zt, const int32_t *izt,
-                         const KLane &k, int lane) {
+template <int LEVEL, int P>
+__device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t *sk, int32_t *scratch,
+                         GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar,
+                         int lane) {
     using V = Lv<LEVEL>;
-    using S = Scratch<LEVEL>;
     int32_t r[8], a[8], acc[8];
     // (rho, rho', K) = H(zeta)  (Alg 1 l.2)
-    stage_bytes(ws.hb, seed, 32, lane);
-    __syncwarp();
-    uint32_t lo = 0, hi = 0;
-    absorb_smem(lo, hi, k, ws.hb, 32, 136, lane);
-    squeeze_words(lo, hi, ws.hb, 16, lane);
-    __syncwarp();
-    if (lane < 32) {
-        uint8_t rb = ws.hb[lane], kb = ws.hb[96 + lane];
-        ws.rho[lane] = rb;
+    if (g == 0) {
+        stage_bytes(gs.hb, seed, 32, lane);
+        __syncwarp();
+        uint32_t lo = 0, hi = 0;
+        absorb_smem(lo, hi, gs.hb, 32, 136, lane);
+        squeeze_words(lo, hi, gs.hb, 16, lane);
+        __syncwarp();
+        uint8_t rb = gs.hb[lane], kb = gs.hb[96 + lane];
+        gs.rho[lane] = rb;
         pk[lane] = rb;
         sk[lane] = rb;
         sk[32 + lane] = kb;
-        ws.rhop[lane] = ws.hb[32 + lane];
-        ws.rhop[32 + lane] = ws.hb[64 + lane];
+        gs.rhop[lane] = gs.hb[32 + lane];
+        gs.rhop[32 + lane] = gs.hb[64 + lane];
     }
-    __syncwarp();
+    group_sync<P>(bar);
     // s1: sample, pack into sk, NTT  (l.4)
-    for (int j = 0; j < V::L; ++j) {
-        expand_s_poly<V::ETA>(ws.rhop, j, ws.buf, ws.sq, k, lane);
+    constexpr int U1 = Units<V::L, P>::SIZE;
+    for (int j = U1 * g; j < V::L; j += U1 * P) {
+        const bool two = U1 == 2 && j + 1 < V::L;
+        if (two)
+            expand_s_pair<V::ETA>(gs.rhop, j, j + 1, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
+        else
+            expand_s_poly<V::ETA>(gs.rhop, j, ws.buf2, ws.sq, lane);
+        for (int h = two ? 0 : 1; h < 2; ++h) {
+            const int32_t *src = h ? ws.buf2 : ws.buf;
+            const int jj = two ? j + h : j;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) a[m] = ws.buf[8 * lane + m + 4 * (lane >> 2)];
-        pack_seq<V::ETABITS>(sk + V::SK_S1 + j * V::POLYETA, a, V::ETA, -1, lane);
-        read_buf_l0(r, ws.buf, lane);
-        __syncwarp();
-        ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(scratch + j * N, r, lane);
-    }
-    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)  (l.3, l.5, l.6)
-    for (int i = 0; i < V::K; ++i) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) acc[m] = 0;
-        for (int j = 0; j < V::L; ++j) {
-            expand_a_poly(ws.rho, i, j, ws.buf, ws.sq, k, lane);
-            read_buf_l2(a, ws.buf, lane);
+            for (int m = 0; m < 8; ++m) a[m] = src[8 * lane + m + 4 * (lane >> 2)];
+            pack_seq<V::ETABITS>(sk + V::SK_S1 + jj * V::POLYETA, a, V::ETA, -1, lane);
+            read_buf_l0(r, src, lane);
             __syncwarp();
-            load_l2(r, scratch + j * N, lane);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], r[m]);
+            ntt_fwd(r, ws.buf, zt, lane);
+            store_l2(scratch + jj * N, r, lane);
         }
+    }
+    group_sync<P>(bar);
+    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)  (l.3, l.5, l.6)
+    for (int i = g; i < V::K; i += P) {
+        accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = reduce_q(acc[m]);
         ntt_inv(acc, ws.buf, izt, lane);
-        expand_s_poly<V::ETA>(ws.rhop, V::L + i, ws.buf, ws.sq, k, lane);
+        expand_s_poly<V::ETA>(gs.rhop, V::L + i, ws.buf, ws.sq, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) a[m] = ws.buf[8 * lane + m + 4 * (lane >> 2)];
         pack_seq<V::ETABITS>(sk + V::SK_S2 + i * V::POLYETA, a, V::ETA, -1, lane);
@@ -169,99 +254,118 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
         l0_to_seq(t0, ws.buf, lane);
         pack_seq<D>(sk + V::SK_T0 + i * V::POLYT0, t0, 1 << (D - 1), -1, lane);
     }
-    __syncwarp();
     __threadfence_block();
+    group_sync<P>(bar);
     // tr = H(rho || t1)  (l.7)
-    lo = 0;
-    hi = 0;
-    absorb_concat(lo, hi, k, ws.hb, 0, pk, V::PK, 136, lane);
-    if (lane < 4) {
+    if (g == 0) {
+        uint32_t lo = 0, hi = 0;
+        absorb_concat(lo, hi, gs.hb, 0, pk, V::PK, 136, lane);
+        if (lane < 4) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sk[64 + 8 * lane + q] = (uint8_t)((q < 4 ? lo : hi) >> (8 * (q & 3)));
+            for (int q = 0; q < 8; ++q) sk[64 + 8 * lane + q] = (uint8_t)((q < 4 ? lo : hi) >> (8 * (q & 3)));
+        }
     }
 }
 
 // -------------------------------------------------------------------------
-// Alg 2: Sign.  Returns 0 on success, -5 when max_iter repetitions rejected.
-// scratch: SIGN_POLYS polys.  *iters receives the number of repetitions.
+// Alg 2: Sign
 // -------------------------------------------------------------------------
 
 // Precomputation shared by every repetition: mu, rho', A^, s^1, s^2, t^0.
-template <int LEVEL>
+template <int LEVEL, int P>
 __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__restrict__ msg, size_t mlen,
-                             int32_t *__restrict__ scratch, WarpSmem &ws, const int32_t *zt, const KLane &k,
+                             int32_t *scratch, GroupSmem &gs, WarpSmem &ws, const int32_t *zt, int g, int bar,
                              int lane) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     int32_t r[8];
-    if (lane < 32) {
-        ws.rho[lane] = __ldg(sk + lane);
-        ws.hb[HB_K + lane] = __ldg(sk + 32 + lane);
-        ws.tr[lane] = __ldg(sk + 64 + lane);
+    if (g == 0) {
+        gs.rho[lane] = __ldg(sk + lane);
+        gs.hb[HB_K + lane] = __ldg(sk + 32 + lane);
+        gs.tr[lane] = __ldg(sk + 64 + lane);
     }
-    __syncwarp();
-    // mu = H(tr || M)  (Alg 2 l.1)
-    uint32_t lo = 0, hi = 0;
-    absorb_concat(lo, hi, k, ws.tr, 32, msg, mlen, 136, lane);
-    squeeze_words(lo, hi, ws.hb + HB_MU, 8, lane);
-    __syncwarp();
-    // rho' = H(K || mu)  (l.2)
-    lo = 0;
-    hi = 0;
-    absorb_smem(lo, hi, k, ws.hb + HB_K, 96, 136, lane);
-    squeeze_words(lo, hi, ws.rhop, 8, lane);
-    __syncwarp();
-    // A^ = ExpandA(rho)  (l.3)
-    for (int i = 0; i < V::K; ++i)
-        for (int j = 0; j < V::L; ++j) {
-            expand_a_poly(ws.rho, i, j, ws.buf, ws.sq, k, lane);
-            int32_t a[8];
-            read_buf_l2(a, ws.buf, lane);
-            __syncwarp();
-            store_l2(scratch + (S::AH + i * V::L + j) * N, a, lane);
+    group_sync<P>(bar);
+    if (g == 0) {
+        // mu = H(tr || M)  (Alg 2 l.1)
+        uint32_t lo = 0, hi = 0;
+        absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
+        squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        __syncwarp();
+        // rho' = H(K || mu)  (l.2)
+        lo = 0;
+        hi = 0;
+        absorb_smem(lo, hi, gs.hb + HB_K, 96, 136, lane);
+        squeeze_words(lo, hi, gs.rhop, 8, lane);
+        __syncwarp();
+    }
+    // A^ = ExpandA(rho)  (l.3); k l is even, so units are pairs when P allows
+    constexpr int KL = V::K * V::L;
+    constexpr int UA = Units<KL, P>::SIZE;
+    for (int p = UA * g; p < KL; p += UA * P) {
+        int32_t a[8];
+        if (UA == 2) {
+            expand_a_pair(gs.rho, p / V::L, p % V::L, (p + 1) / V::L, (p + 1) % V::L, ws.buf, ws.buf2, ws.sq,
+                          ws.sq2, lane);
+            read_buf_l2(a, ws.buf2, lane);
+            store_l2(scratch + (S::AH + p + 1) * N, a, lane);
+        } else {
+            expand_a_poly(gs.rho, p / V::L, p % V::L, ws.buf, ws.sq, lane);
         }
-    // s^1, s^2, t^0  (l.4)
-    for (int j = 0; j < V::L; ++j) {
-        unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S1 + j * V::POLYETA, V::ETA, ws, lane);
-        ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(scratch + (S::S1H + j) * N, r, lane);
+        read_buf_l2(a, ws.buf, lane);
+        store_l2(scratch + (S::AH + p) * N, a, lane);
+        __syncwarp();
     }
-    for (int i = 0; i < V::K; ++i) {
-        unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S2 + i * V::POLYETA, V::ETA, ws, lane);
+    // s^1, s^2, t^0  (l.4): polynomials u = 0 .. l + 2k - 1 across the group
+    for (int u = g; u < V::L + 2 * V::K; u += P) {
+        if (u < V::L) {
+            unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S1 + u * V::POLYETA, V::ETA, ws, lane);
+        } else if (u < V::L + V::K) {
+            unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S2 + (u - V::L) * V::POLYETA, V::ETA, ws, lane);
+        } else {
+            unpack_poly_l0<D>(r, sk + V::SK_T0 + (u - V::L - V::K) * V::POLYT0, 1 << (D - 1), ws, lane);
+        }
         ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(scratch + (S::S2H + i) * N, r, lane);
+        store_l2(scratch + (S::S1H + u) * N, r, lane);   // S1H, S2H, T0H are contiguous
     }
-    for (int i = 0; i < V::K; ++i) {
-        unpack_poly_l0<D>(r, sk + V::SK_T0 + i * V::POLYT0, 1 << (D - 1), ws, lane);
-        ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(scratch + (S::T0H + i) * N, r, lane);
-    }
+    group_sync<P>(bar);
 }
 
 // One repetition of the rejection loop with nonce base kappa (l.6-18), with
 // early evaluation: each polynomial is checked as soon as it is produced.
-// Returns true when (z, h) is accepted; then ws.ctilde, scratch Z and ws.hmask
-// hold the signature parts.
-template <int LEVEL>
-__device__ bool sign_attempt(int kappa, int32_t *__restrict__ scratch, WarpSmem &ws, const int32_t *zt,
-                             const int32_t *izt, const KLane &k, int lane) {
+// Returns true (on every warp of the group) when (z, h) is accepted; then
+// gs.ctilde, scratch Z and gs.hmask hold the signature parts.
+// pre: the task's precomputation part (possibly prepared by another warp
+// group, so it is read through L2); itr: this worker's per-repetition part.
+template <int LEVEL, int P>
+__device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws,
+                             const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
+    volatile int *vflag = &gs.flag;
     int32_t r[8], a[8], acc[8], ch[8];
     // y = ExpandMask(rho', kappa); y^ = NTT(y)  (l.6)
-    for (int j = 0; j < V::L; ++j) {
-        expand_mask_poly<V::ZBITS, V::GAMMA1>(ws.rhop, kappa + j, r, ws.sq, k, lane);
-        store_l0(scratch + (S::Y + j) * N, r, lane);
+    constexpr int UY = Units<V::L, P>::SIZE;
+    for (int j = UY * g; j < V::L; j += UY * P) {
+        if (UY == 2 && j + 1 < V::L) {
+            expand_mask_pair<V::ZBITS, V::GAMMA1>(gs.rhop, kappa + j, kappa + j + 1, r, a, ws.sq, ws.sq2, lane);
+            store_l0(itr + (S::Y + j + 1) * N, a, lane);
+            ntt_fwd(a, ws.buf, zt, lane);
+            store_l2(itr + (S::YH + j + 1) * N, a, lane);
+        } else {
+            expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa + j, r, ws.sq, lane);
+        }
+        store_l0(itr + (S::Y + j) * N, r, lane);
         ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(scratch + (S::YH + j) * N, r, lane);
+        store_l2(itr + (S::YH + j) * N, r, lane);
     }
+    group_sync<P>(bar);
     // w = INTT(A^ o y^); w1 = HighBits(w)  (l.7-8)
-    for (int i = 0; i < V::K; ++i) {
+    for (int i = g; i < V::K; i += P) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = 0;
         for (int j = 0; j < V::L; ++j) {
-            load_l2(a, scratch + (S::AH + i * V::L + j) * N, lane);
-            load_l2(r, scratch + (S::YH + j) * N, lane);
+            load_l2_cg(a, pre + (S::AH + i * V::L + j) * N, lane);
+            load_l2(r, itr + (S::YH + j) * N, lane);
 #pragma unroll
             for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], r[m]);
         }
@@ -273,46 +377,50 @@ __device__ bool sign_attempt(int kappa, int32_t *__restrict__ scratch, WarpSmem 
             acc[m] = to_canonical(acc[m]);
             r[m] = highbits<LEVEL>(acc[m]);
         }
-        store_l0(scratch + (S::W + i) * N, acc, lane);
+        store_l0(itr + (S::W + i) * N, acc, lane);
         l0_to_seq(r, ws.buf, lane);
-        pack_seq<V::W1BITS>(ws.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
+        pack_seq<V::W1BITS>(gs.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
     }
-    __syncwarp();
+    group_sync<P>(bar);
     // c~ = H(mu || w1)  (l.9)
-    {
+    if (g == 0) {
         uint32_t lo = 0, hi = 0;
-        absorb_smem(lo, hi, k, ws.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
-        squeeze_words(lo, hi, ws.ctilde, 4, lane);
-        __syncwarp();
+        absorb_smem(lo, hi, gs.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
+        squeeze_words(lo, hi, gs.ctilde, 4, lane);
+        if (lane == 0) {
+            gs.flag = 0;
+            gs.count = 0;
+        }
     }
-    // c = SampleInBall(c~); c^ = NTT(c)  (l.10)
-    sample_in_ball<V::TAU>(ws.ctilde, ws.buf, ws.sq, k, lane);
-    read_buf_l0(ch, ws.buf, lane);
-    __syncwarp();
-    ntt_fwd(ch, ws.buf, zt, lane);
+    group_sync<P>(bar);
+    // c^ = NTT(SampleInBall(c~))  (l.10)
+    challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta  (l.11, l.14)
-    for (int j = 0; j < V::L; ++j) {
-        load_l2(a, scratch + (S::S1H + j) * N, lane);
+    for (int j = g; j < V::L && !*vflag; j += P) {
+        load_l2_cg(a, pre + (S::S1H + j) * N, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) r[m] = mont_mul(ch[m], a[m]);
         ntt_inv(r, ws.buf, izt, lane);
-        load_l0(a, scratch + (S::Y + j) * N, lane);
+        load_l0(a, itr + (S::Y + j) * N, lane);
         bool bad = false;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             r[m] = centre_small(to_canonical(r[m]) + a[m]);
             bad |= iabs(r[m]) >= V::GAMMA1 - V::BETA;
         }
-        if (__any_sync(FULL, bad)) return false;
-        store_l0(scratch + (S::Z + j) * N, r, lane);
+        if (__any_sync(FULL, bad)) {
+            if (lane == 0) *vflag = 1;
+            break;
+        }
+        store_l0(itr + (S::Z + j) * N, r, lane);
     }
     // v_s = INTT(c^ o s^2); r0 = LowBits(w - v_s)  (l.12-14)
-    for (int i = 0; i < V::K; ++i) {
-        load_l2(a, scratch + (S::S2H + i) * N, lane);
+    for (int i = g; i < V::K && !*vflag; i += P) {
+        load_l2_cg(a, pre + (S::S2H + i) * N, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) r[m] = mont_mul(ch[m], a[m]);
         ntt_inv(r, ws.buf, izt, lane);
-        load_l0(a, scratch + (S::W + i) * N, lane);
+        load_l0(a, itr + (S::W + i) * N, lane);
         bool bad = false;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -324,17 +432,21 @@ __device__ bool sign_attempt(int kappa, int32_t *__restrict__ scratch, WarpSmem 
             bad |= iabs(l0) >= V::GAMMA2 - V::BETA;
             a[m] = d;
         }
-        if (__any_sync(FULL, bad)) return false;
-        store_l0(scratch + (S::W + i) * N, a, lane);  // keep w - c s2 for the hint
+        if (__any_sync(FULL, bad)) {
+            if (lane == 0) *vflag = 1;
+            break;
+        }
+        store_l0(itr + (S::W + i) * N, a, lane);  // keep w - c s2 for the hint
     }
+    group_sync<P>(bar);
+    if (*vflag) return false;
     // v_t = INTT(c^ o t^0); h = MakeHint(-v_t, w - v_s + v_t)  (l.17-19)
-    int count = 0;
-    for (int i = 0; i < V::K; ++i) {
-        load_l2(a, scratch + (S::T0H + i) * N, lane);
+    for (int i = g; i < V::K && !*vflag; i += P) {
+        load_l2_cg(a, pre + (S::T0H + i) * N, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) r[m] = mont_mul(ch[m], a[m]);
         ntt_inv(r, ws.buf, izt, lane);
-        load_l0(a, scratch + (S::W + i) * N, lane);
+        load_l0(a, itr + (S::W + i) * N, lane);
         bool bad = false;
         uint32_t hbits = 0;
 #pragma unroll
@@ -346,37 +458,41 @@ __device__ bool sign_attempt(int kappa, int32_t *__restrict__ scratch, WarpSmem 
             int32_t z = vt ? Q - vt : 0;
             hbits |= (uint32_t)make_hint<LEVEL>(z, rr) << m;
         }
-        if (__any_sync(FULL, bad)) return false;
+        if (__any_sync(FULL, bad)) {
+            if (lane == 0) *vflag = 1;
+            break;
+        }
+        int count = 0;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             uint32_t w = __ballot_sync(FULL, (hbits >> m) & 1u);
-            if (lane == 0) ws.hmask[i * 8 + m] = w;
+            if (lane == 0) gs.hmask[i * 8 + m] = w;
             count += __popc(w);
         }
-        if (count > V::OMEGA) return false;
+        if (lane == 0) atomicAdd(&gs.count, count);
     }
-    __syncwarp();
-    return true;
+    group_sync<P>(bar);
+    return !*vflag && gs.count <= V::OMEGA;
 }
 
 // Writes sig = c~ || z (gamma1 - z in ZBITS bits) || h (indices, then counts).
-template <int LEVEL>
-__device__ void sign_pack(uint8_t *__restrict__ sig, const int32_t *__restrict__ scratch, const WarpSmem &ws,
-                          int lane) {
+template <int LEVEL, int P>
+__device__ void sign_pack(uint8_t *sig, const int32_t *itr, const GroupSmem &gs, int g, int lane) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
-    sig[lane] = ws.ctilde[lane];
-    for (int j = 0; j < V::L; ++j) {
+    for (int j = g; j < V::L; j += P) {
         int32_t v[8];
-        load_l2(v, scratch + (S::Z + j) * N, lane);   // 8 consecutive coefficients
+        load_l2(v, itr + (S::Z + j) * N, lane);   // 8 consecutive coefficients
         pack_seq<V::ZBITS>(sig + V::SIG_Z + j * V::POLYZ, v, V::GAMMA1, -1, lane);
     }
+    if (g != P - 1) return;
+    sig[lane] = gs.ctilde[lane];
     uint8_t *h = sig + V::SIG_H;
     int base = 0;
     for (int i = 0; i < V::K; ++i) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            uint32_t w = ws.hmask[i * 8 + m];
+            uint32_t w = gs.hmask[i * 8 + m];
             if ((w >> lane) & 1u) h[base + __popc(w & lanemask_lt(lane))] = (uint8_t)(lane + 32 * m);
             base += __popc(w);
         }
@@ -385,30 +501,31 @@ __device__ void sign_pack(uint8_t *__restrict__ sig, const int32_t *__restrict__
     for (int p = base + lane; p < V::OMEGA; p += 32) h[p] = 0;
 }
 
-template <int LEVEL>
-__device__ void sign_zero(uint8_t *__restrict__ sig, int lane) {
-    for (int p = lane; p < Lv<LEVEL>::SIG; p += 32) sig[p] = 0;
+template <int LEVEL, int P>
+__device__ void sign_zero(uint8_t *sig, int g, int lane) {
+    for (int p = 32 * g + lane; p < Lv<LEVEL>::SIG; p += 32 * P) sig[p] = 0;
 }
 
 // -------------------------------------------------------------------------
-// Alg 3: Verify.  Returns 1 (accept) or 0.  scratch: VERIFY_POLYS polys.
+// Alg 3: Verify.  Returns 1 (accept) or 0 on every warp of the group.
+// scratch: VERIFY_POLYS polys.
 // -------------------------------------------------------------------------
-template <int LEVEL>
+template <int LEVEL, int P>
 __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__restrict__ msg, size_t mlen,
-                           const uint8_t *__restrict__ sig, int32_t *__restrict__ scratch, WarpSmem &ws,
-                           const int32_t *zt, const int32_t *izt, const KLane &k, int lane) {
+                           const uint8_t *__restrict__ sig, int32_t *scratch, GroupSmem &gs, WarpSmem &ws,
+                           const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
     using V = Lv<LEVEL>;
-    int32_t r[8], a[8], acc[8], ch[8];
-    // c~ and rho
-    ws.ctilde[lane] = __ldg(sig + lane);
-    ws.rho[lane] = __ldg(pk + lane);
-    // strict hint decoding into bit masks
-    stage_bytes(ws.sq, sig + V::SIG_H, V::OMEGA + V::K, lane);
-    ws.hmask[lane] = 0;
-    ws.hmask[32 + lane] = 0;
-    __syncwarp();
-    bool bad = false;
-    {
+    volatile int *vflag = &gs.flag;
+    int32_t r[8], acc[8], ch[8];
+    if (g == 0) {
+        gs.ctilde[lane] = __ldg(sig + lane);
+        gs.rho[lane] = __ldg(pk + lane);
+        // strict hint decoding into bit masks
+        stage_bytes(ws.sq, sig + V::SIG_H, V::OMEGA + V::K, lane);
+        gs.hmask[lane] = 0;
+        gs.hmask[32 + lane] = 0;
+        __syncwarp();
+        bool bad = false;
         int prev = 0;
         for (int i = 0; i < V::K; ++i) {
             int end = ws.sq[V::OMEGA + i];
@@ -419,54 +536,49 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
             for (int j = prev + lane; j < end; j += 32) {
                 int idx = ws.sq[j];
                 if (j > prev && idx <= ws.sq[j - 1]) bad = true;
-                atomicOr(&ws.hmask[i * 8 + (idx >> 5)], 1u << (idx & 31));
+                atomicOr(&gs.hmask[i * 8 + (idx >> 5)], 1u << (idx & 31));
             }
             prev = end;
         }
         if (!bad)
             for (int j = prev + lane; j < V::OMEGA; j += 32)
                 if (ws.sq[j]) bad = true;
+        bad = __any_sync(FULL, bad);
+        if (lane == 0) gs.flag = bad ? 1 : 0;
     }
-    bad = __any_sync(FULL, bad);
-    __syncwarp();
-    if (bad) return 0;
+    group_sync<P>(bar);
+    if (*vflag) return 0;
     // z: unpack, ||z|| < gamma1 - beta, z^ = NTT(z)  (Alg 3 l.6 first term, l.4)
-    for (int j = 0; j < V::L; ++j) {
+    for (int j = g; j < V::L && !*vflag; j += P) {
         unpack_poly_l0<V::ZBITS>(r, sig + V::SIG_Z + j * V::POLYZ, V::GAMMA1, ws, lane);
         bool b = false;
 #pragma unroll
         for (int m = 0; m < 8; ++m) b |= iabs(r[m]) >= V::GAMMA1 - V::BETA;
-        if (__any_sync(FULL, b)) return 0;
+        if (__any_sync(FULL, b)) {
+            if (lane == 0) *vflag = 1;
+            break;
+        }
         ntt_fwd(r, ws.buf, zt, lane);
         store_l2(scratch + j * N, r, lane);
     }
-    // mu = H(H(rho || t1) || M)  (l.2)
-    uint32_t lo = 0, hi = 0;
-    absorb_concat(lo, hi, k, ws.tr, 0, pk, V::PK, 136, lane);
-    squeeze_words(lo, hi, ws.tr, 4, lane);
-    __syncwarp();
-    lo = 0;
-    hi = 0;
-    absorb_concat(lo, hi, k, ws.tr, 32, msg, mlen, 136, lane);
-    squeeze_words(lo, hi, ws.hb + HB_MU, 8, lane);
-    __syncwarp();
+    // mu = H(H(rho || t1) || M)  (l.2), on the last warp
+    if (g == P - 1) {
+        uint32_t lo = 0, hi = 0;
+        absorb_concat(lo, hi, gs.tr, 0, pk, V::PK, 136, lane);
+        squeeze_words(lo, hi, gs.tr, 4, lane);
+        __syncwarp();
+        lo = 0;
+        hi = 0;
+        absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
+        squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+    }
+    group_sync<P>(bar);
+    if (*vflag) return 0;
     // c^ = NTT(SampleInBall(c~))  (l.3)
-    sample_in_ball<V::TAU>(ws.ctilde, ws.buf, ws.sq, k, lane);
-    read_buf_l0(ch, ws.buf, lane);
-    __syncwarp();
-    ntt_fwd(ch, ws.buf, zt, lane);
+    challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)  (l.4-5)
-    for (int i = 0; i < V::K; ++i) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) acc[m] = 0;
-        for (int j = 0; j < V::L; ++j) {
-            expand_a_poly(ws.rho, i, j, ws.buf, ws.sq, k, lane);
-            read_buf_l2(a, ws.buf, lane);
-            __syncwarp();
-            load_l2(r, scratch + j * N, lane);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], r[m]);
-        }
+    for (int i = g; i < V::K; i += P) {
+        accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
         unpack_poly_l0<10>(r, pk + 32 + i * V::POLYT1, 0, ws, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) r[m] = (-r[m]) << D;   // t1 2^d, t1 stored as 0 - field
@@ -476,23 +588,27 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         ntt_inv(acc, ws.buf, izt, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            int hbit = (ws.hmask[i * 8 + m] >> lane) & 1u;
+            int hbit = (gs.hmask[i * 8 + m] >> lane) & 1u;
             r[m] = use_hint<LEVEL>(hbit, to_canonical(acc[m]));
         }
         l0_to_seq(r, ws.buf, lane);
-        pack_seq<V::W1BITS>(ws.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
+        pack_seq<V::W1BITS>(gs.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
     }
-    __syncwarp();
+    group_sync<P>(bar);
     // c~ == H(mu || w1')  (l.6)
-    lo = 0;
-    hi = 0;
-    absorb_smem(lo, hi, k, ws.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
-    bool eq = true;
-    if (lane < 4) {
-        uint2 w = *reinterpret_cast<const uint2 *>(ws.ctilde + 8 * lane);
-        eq = (w.x == lo) && (w.y == hi);
+    if (g == 0) {
+        uint32_t lo = 0, hi = 0;
+        absorb_smem(lo, hi, gs.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
+        bool eq = true;
+        if (lane < 4) {
+            uint2 w = *reinterpret_cast<const uint2 *>(gs.ctilde + 8 * lane);
+            eq = (w.x == lo) && (w.y == hi);
+        }
+        eq = __all_sync(FULL, eq);
+        if (lane == 0) gs.flag = eq ? 0 : 1;
     }
-    return __all_sync(FULL, eq) ? 1 : 0;
+    group_sync<P>(bar);
+    return *vflag ? 0 : 1;
 }
 
 }  // namespace dil

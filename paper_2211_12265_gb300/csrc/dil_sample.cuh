@@ -1,6 +1,8 @@
 // Warp-level samplers (section 2.3 "Sampling"; section 3.4 / Alg 4 of
 // arXiv 2211.12265: rejection sampling with a warp vote of the accept bits, an
 // inclusive popcount for each lane's write offset and a running count).
+// The *_pair variants run two independent sponges through the interleaved
+// permutation (keccak_f2), for instruction-level parallelism.
 #pragma once
 #include "dil_keccak.cuh"
 #include "dil_ntt.cuh"
@@ -22,97 +24,178 @@ __device__ __forceinline__ uint32_t get_field(const uint8_t *buf, int pos, int b
     return v & ((1u << bits) - 1u);
 }
 
-// ExpandA: A^_ij from SHAKE128(rho || j || i).  Candidates are 3-byte
-// little-endian words with the top bit cleared, kept when < q, in stream order;
-// coefficient c is written to buf[c + (c >> 3)] (layout for an L2 read).
+// ---------------------------------------------------------------- ExpandA
+// A^_ij from SHAKE128(rho || j || i).  Candidates are 3-byte little-endian
+// words with the top bit cleared, kept when < q, in stream order; coefficient
+// c is written to buf[c + (c >> 3)] (layout for an L2 read).
+
+// Rejection step over one squeezed 168-byte block (56 candidates).
+__device__ __forceinline__ int expand_a_block(const uint8_t *sq, int32_t *buf, int ctr, int lane) {
+#pragma unroll
+    for (int rnd = 0; rnd < 2; ++rnd) {
+        int c = rnd * 32 + lane;
+        bool valid = c < 56;
+        uint32_t v = valid ? (get_field(sq, 24 * c, 24) & 0x7FFFFFu) : 0u;
+        bool acc = valid && v < (uint32_t)Q;
+        uint32_t mask = __ballot_sync(FULL, acc);
+        int pos = ctr + __popc(mask & lanemask_lt(lane));
+        if (acc && pos < N) buf[pos + (pos >> 3)] = (int32_t)v;
+        ctr += __popc(mask);
+    }
+    return ctr;
+}
+
 // rho: 32 bytes in shared memory (8-byte aligned); sq: >= 176-byte scratch.
 __device__ __forceinline__ void expand_a_poly(const uint8_t *rho, int i, int j, int32_t *buf, uint8_t *sq,
-                                              const KLane &k, int lane) {
+                                              int lane) {
     uint32_t lo, hi;
-    absorb_seed(lo, hi, k, rho, 4, (uint32_t)j | ((uint32_t)i << 8), 2, 168, lane);
+    absorb_seed(lo, hi, rho, 4, (uint32_t)j | ((uint32_t)i << 8), 2, 168, lane);
     int ctr = 0;
-    // bounded: a correct stream needs 5 or 6 blocks; 64 is unreachable in practice
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo, hi, sq, 21, lane);
         __syncwarp();
-#pragma unroll
-        for (int rnd = 0; rnd < 2; ++rnd) {
-            int c = rnd * 32 + lane;
-            bool valid = c < 56;
-            uint32_t v = valid ? (get_field(sq, 24 * c, 24) & 0x7FFFFFu) : 0u;
-            bool acc = valid && v < (uint32_t)Q;
-            uint32_t mask = __ballot_sync(FULL, acc);
-            int pos = ctr + __popc(mask & lanemask_lt(lane));
-            if (acc && pos < N) buf[pos + (pos >> 3)] = (int32_t)v;
-            ctr += __popc(mask);
-        }
+        ctr = expand_a_block(sq, buf, ctr, lane);
         __syncwarp();
         if (ctr >= N) break;
-        keccak_f(lo, hi, k);
+        keccak_f(lo, hi);
     }
 }
 
-// ExpandS: one polynomial with coefficients in [-eta, eta] from
-// SHAKE256(rho' || nonce); each byte gives two 4-bit candidates, low first.
-// Coefficient c is written to buf[c + 4 (c >> 5)] (layout for an L0 read).
+// A^_{i0 j0} into buf0 and A^_{i1 j1} into buf1.
+__device__ __forceinline__ void expand_a_pair(const uint8_t *rho, int i0, int j0, int i1, int j1, int32_t *buf0,
+                                              int32_t *buf1, uint8_t *sq0, uint8_t *sq1, int lane) {
+    uint32_t lo0, hi0, lo1, hi1;
+    seed_words(lo0, hi0, rho, 4, (uint32_t)j0 | ((uint32_t)i0 << 8), 2, 168, lane);
+    seed_words(lo1, hi1, rho, 4, (uint32_t)j1 | ((uint32_t)i1 << 8), 2, 168, lane);
+    keccak_f2(lo0, hi0, lo1, hi1);
+    int c0 = 0, c1 = 0;
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+        squeeze_words(lo0, hi0, sq0, 21, lane);
+        squeeze_words(lo1, hi1, sq1, 21, lane);
+        __syncwarp();
+        if (c0 < N) c0 = expand_a_block(sq0, buf0, c0, lane);
+        if (c1 < N) c1 = expand_a_block(sq1, buf1, c1, lane);
+        __syncwarp();
+        if (c0 >= N && c1 >= N) break;
+        keccak_f2(lo0, hi0, lo1, hi1);
+    }
+}
+
+// ---------------------------------------------------------------- ExpandS
+// One polynomial with coefficients in [-eta, eta] from SHAKE256(rho' || nonce);
+// each byte gives two 4-bit candidates, low first.  Coefficient c is written
+// to buf[c + 4 (c >> 5)] (layout for an L0 read).
+
 template <int ETA>
-__device__ __forceinline__ void expand_s_poly(const uint8_t *rhop, int nonce, int32_t *buf, uint8_t *sq,
-                                              const KLane &k, int lane) {
+__device__ __forceinline__ int expand_s_block(const uint8_t *sq, int32_t *buf, int ctr, int lane) {
+#pragma unroll
+    for (int rnd = 0; rnd < 5; ++rnd) {
+        int c = rnd * 32 + lane;
+        bool valid = c < 136;
+        uint32_t byte = valid ? sq[c] : 0xFFu;
+        uint32_t t0 = byte & 15u, t1 = byte >> 4;
+        bool a0 = valid && (ETA == 2 ? t0 < 15u : t0 < 9u);
+        bool a1 = valid && (ETA == 2 ? t1 < 15u : t1 < 9u);
+        uint32_t m0 = __ballot_sync(FULL, a0), m1 = __ballot_sync(FULL, a1);
+        uint32_t lt = lanemask_lt(lane);
+        int pos0 = ctr + __popc(m0 & lt) + __popc(m1 & lt);
+        int pos1 = pos0 + (a0 ? 1 : 0);
+        if (a0 && pos0 < N) buf[pos0 + 4 * (pos0 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t0 % 5u) : 4 - (int32_t)t0;
+        if (a1 && pos1 < N) buf[pos1 + 4 * (pos1 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t1 % 5u) : 4 - (int32_t)t1;
+        ctr += __popc(m0) + __popc(m1);
+    }
+    return ctr;
+}
+
+template <int ETA>
+__device__ __forceinline__ void expand_s_poly(const uint8_t *rhop, int nonce, int32_t *buf, uint8_t *sq, int lane) {
     uint32_t lo, hi;
-    absorb_seed(lo, hi, k, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
+    absorb_seed(lo, hi, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
     int ctr = 0;
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo, hi, sq, 17, lane);
         __syncwarp();
-#pragma unroll
-        for (int rnd = 0; rnd < 5; ++rnd) {
-            int c = rnd * 32 + lane;
-            bool valid = c < 136;
-            uint32_t byte = valid ? sq[c] : 0xFFu;
-            uint32_t t0 = byte & 15u, t1 = byte >> 4;
-            bool a0 = valid && (ETA == 2 ? t0 < 15u : t0 < 9u);
-            bool a1 = valid && (ETA == 2 ? t1 < 15u : t1 < 9u);
-            uint32_t m0 = __ballot_sync(FULL, a0), m1 = __ballot_sync(FULL, a1);
-            uint32_t lt = lanemask_lt(lane);
-            int pos0 = ctr + __popc(m0 & lt) + __popc(m1 & lt);
-            int pos1 = pos0 + (a0 ? 1 : 0);
-            if (a0 && pos0 < N) buf[pos0 + 4 * (pos0 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t0 % 5u) : 4 - (int32_t)t0;
-            if (a1 && pos1 < N) buf[pos1 + 4 * (pos1 >> 5)] = (ETA == 2) ? 2 - (int32_t)(t1 % 5u) : 4 - (int32_t)t1;
-            ctr += __popc(m0) + __popc(m1);
-        }
+        ctr = expand_s_block<ETA>(sq, buf, ctr, lane);
         __syncwarp();
         if (ctr >= N) break;
-        keccak_f(lo, hi, k);
+        keccak_f(lo, hi);
     }
 }
 
-// ExpandMask: y = gamma1 - t for consecutive ZBITS-bit fields t of
-// SHAKE256(rho' || nonce).  Returns the polynomial in layout L0.
+template <int ETA>
+__device__ __forceinline__ void expand_s_pair(const uint8_t *rhop, int nonce0, int nonce1, int32_t *buf0,
+                                              int32_t *buf1, uint8_t *sq0, uint8_t *sq1, int lane) {
+    uint32_t lo0, hi0, lo1, hi1;
+    seed_words(lo0, hi0, rhop, 8, (uint32_t)nonce0 & 0xFFFFu, 2, 136, lane);
+    seed_words(lo1, hi1, rhop, 8, (uint32_t)nonce1 & 0xFFFFu, 2, 136, lane);
+    keccak_f2(lo0, hi0, lo1, hi1);
+    int c0 = 0, c1 = 0;
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+        squeeze_words(lo0, hi0, sq0, 17, lane);
+        squeeze_words(lo1, hi1, sq1, 17, lane);
+        __syncwarp();
+        if (c0 < N) c0 = expand_s_block<ETA>(sq0, buf0, c0, lane);
+        if (c1 < N) c1 = expand_s_block<ETA>(sq1, buf1, c1, lane);
+        __syncwarp();
+        if (c0 >= N && c1 >= N) break;
+        keccak_f2(lo0, hi0, lo1, hi1);
+    }
+}
+
+// ---------------------------------------------------------------- ExpandMask
+// y = gamma1 - t for consecutive ZBITS-bit fields t of SHAKE256(rho' || nonce).
+// Results are in layout L0.  sq holds 5 x 136 squeezed bytes (+ slack).
+
+template <int ZBITS>
+constexpr int mask_blocks() { return (N * ZBITS / 8 + 135) / 136; }
+
+template <int ZBITS, int32_t GAMMA1>
+__device__ __forceinline__ void mask_extract(const uint8_t *sq, int32_t r[8], int lane) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = GAMMA1 - (int32_t)get_field(sq, ZBITS * (lane + 32 * m), ZBITS);
+}
+
 template <int ZBITS, int32_t GAMMA1>
 __device__ __forceinline__ void expand_mask_poly(const uint8_t *rhop, int nonce, int32_t r[8], uint8_t *sq,
-                                                 const KLane &k, int lane) {
+                                                 int lane) {
     uint32_t lo, hi;
-    absorb_seed(lo, hi, k, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
-    constexpr int BLOCKS = (N * ZBITS / 8 + 135) / 136;
+    absorb_seed(lo, hi, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
 #pragma unroll 1
-    for (int blk = 0; blk < BLOCKS; ++blk) {
-        if (blk) keccak_f(lo, hi, k);
+    for (int blk = 0; blk < mask_blocks<ZBITS>(); ++blk) {
+        if (blk) keccak_f(lo, hi);
         squeeze_words(lo, hi, sq + 136 * blk, 17, lane);
     }
     __syncwarp();
-#pragma unroll
-    for (int m = 0; m < 8; ++m) r[m] = GAMMA1 - (int32_t)get_field(sq, ZBITS * (lane + 32 * m), ZBITS);
+    mask_extract<ZBITS, GAMMA1>(sq, r, lane);
     __syncwarp();
 }
 
-// SampleInBall: c with TAU coefficients +-1 from SHAKE256(c~): the first 8
-// bytes give the signs, then for i = 256-TAU .. 255 a byte b <= i is drawn,
-// c_i <- c_b and c_b <- +-1.  Coefficient c is written to buf[c + 4 (c >> 5)].
+template <int ZBITS, int32_t GAMMA1>
+__device__ __forceinline__ void expand_mask_pair(const uint8_t *rhop, int nonce0, int nonce1, int32_t r0[8],
+                                                 int32_t r1[8], uint8_t *sq0, uint8_t *sq1, int lane) {
+    uint32_t lo0, hi0, lo1, hi1;
+    seed_words(lo0, hi0, rhop, 8, (uint32_t)nonce0 & 0xFFFFu, 2, 136, lane);
+    seed_words(lo1, hi1, rhop, 8, (uint32_t)nonce1 & 0xFFFFu, 2, 136, lane);
+#pragma unroll 1
+    for (int blk = 0; blk < mask_blocks<ZBITS>(); ++blk) {
+        keccak_f2(lo0, hi0, lo1, hi1);
+        squeeze_words(lo0, hi0, sq0 + 136 * blk, 17, lane);
+        squeeze_words(lo1, hi1, sq1 + 136 * blk, 17, lane);
+    }
+    __syncwarp();
+    mask_extract<ZBITS, GAMMA1>(sq0, r0, lane);
+    mask_extract<ZBITS, GAMMA1>(sq1, r1, lane);
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- SampleInBall
+// c with TAU coefficients +-1 from SHAKE256(c~): the first 8 bytes give the
+// signs, then for i = 256-TAU .. 255 a byte b <= i is drawn, c_i <- c_b and
+// c_b <- +-1.  Coefficient c is written to buf[c + 4 (c >> 5)].
 template <int TAU>
-__device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *buf, uint8_t *sq, const KLane &k,
-                                               int lane) {
+__device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *buf, uint8_t *sq, int lane) {
     uint32_t lo, hi;
-    absorb_seed(lo, hi, k, ctilde, 4, 0u, 0, 136, lane);
+    absorb_seed(lo, hi, ctilde, 4, 0u, 0, 136, lane);
     squeeze_words(lo, hi, sq, 17, lane);
 #pragma unroll
     for (int m = 0; m < 8; ++m) buf[lane + 36 * m] = 0;
@@ -125,7 +208,7 @@ __device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *b
             if (pos == 136) {
                 if (++blocks > MAX_SQUEEZE_BLOCKS) break;
                 __syncwarp();
-                keccak_f(lo, hi, k);
+                keccak_f(lo, hi);
                 squeeze_words(lo, hi, sq, 17, lane);
                 __syncwarp();
                 pos = 0;
@@ -142,6 +225,7 @@ __device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *b
     __syncwarp();
 }
 
+// ---------------------------------------------------------------- packing
 // Packs 8 consecutive values (each < 2^BITS) into BITS bytes at out
 // (little-endian bit stream).
 template <int BITS>

@@ -1,0 +1,46 @@
+// Plain Sign kernel (Alg 2): one task per group of P warps, whole rejection
+// loop in one launch (section 4.2 single-kernel fusion with early evaluation).
+#include "dil_kern.cuh"
+
+namespace dil {
+
+template <int LEVEL, int P>
+__global__ void __launch_bounds__(256, 4) k_sign(int n, const uint8_t *__restrict__ sk,
+                                                 const uint8_t *__restrict__ msg, const uint64_t *__restrict__ off,
+                                                 uint8_t *sig, int32_t *status, int32_t *iters, int32_t *scratch,
+                                                 int max_iter) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const CtaView v = cta_setup<P>(smem);
+    const int task = blockIdx.x * v.groups + v.group;
+    if (task >= n) return;
+    using V = Lv<LEVEL>;
+    int32_t *scr = scratch + (size_t)task * Scratch<LEVEL>::SIGN_POLYS * N;
+    const uint64_t m0 = off[task], m1 = off[task + 1];
+    sign_prepare<LEVEL, P>(sk + (size_t)task * V::SK, msg + m0, (size_t)(m1 - m0), scr, *v.gs, *v.ws, v.zt, v.g,
+                           v.bar, v.lane);
+    int it = 0;
+    bool ok = false;
+    while (it < max_iter) {
+        ok = sign_attempt<LEVEL, P>(it * V::L, scr, scr + Scratch<LEVEL>::PRE_POLYS * N, *v.gs, *v.ws, v.zt,
+                                    v.izt, v.g, v.bar, v.lane);
+        ++it;
+        if (ok) break;
+    }
+    uint8_t *tsig = sig + (size_t)task * V::SIG;
+    if (ok)
+        sign_pack<LEVEL, P>(tsig, scr + Scratch<LEVEL>::PRE_POLYS * N, *v.gs, v.g, v.lane);
+    else
+        sign_zero<LEVEL, P>(tsig, v.g, v.lane);
+    if (v.g == 0 && v.lane == 0) {
+        if (status) status[task] = ok ? 0 : -5;
+        if (iters) iters[task] = it;
+    }
+}
+
+cudaError_t launch_sign(int level, int n, const uint8_t *sk, const uint8_t *msg, const uint64_t *off,
+                        uint8_t *sig, int32_t *status, int32_t *iters, int32_t *scratch, int max_iter, int warps,
+                        int p, cudaStream_t s) {
+    DIL_DISPATCH(k_sign, sk, msg, off, sig, status, iters, scratch, max_iter)
+}
+
+}  // namespace dil

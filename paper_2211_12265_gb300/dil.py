@@ -51,6 +51,7 @@ def load() -> ctypes.CDLL:
                 "dil_ctx_create": [I, S, P],
                 "dil_ctx_destroy": [P],
                 "dil_set_max_iter": [P, I],
+                "dil_set_tuning": [P, I, I, I],
                 "dil_keygen": [P, I, S, P, P, P, P],
                 "dil_sign": [P, I, S, P, P, P, P, P, P],
                 "dil_sign_ex": [P, I, S, P, P, P, P, P, P, P],
@@ -67,6 +68,9 @@ def load() -> ctypes.CDLL:
                 "dil_test_sample_in_ball": [P, I, S, P, P, P],
                 "dil_test_rounding": [P, I, S, P, P, P, P, P],
                 "dil_test_issue_rate": [P, I, P],
+                "dil_sign_persistent": [P, I, P, P],
+                "dil_set_persistent_tuning": [P, I, I, I, I, I],
+                "dil_persistent_status": [P, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -130,6 +134,10 @@ def dil_ctx_destroy(ctx: int) -> None:
 
 def dil_set_max_iter(ctx: int, max_iter: int) -> None:
     _check(load().dil_set_max_iter(ctx, max_iter), "dil_set_max_iter")
+
+
+def dil_set_tuning(ctx: int, op: int, warps_per_cta: int, warps_per_task: int = 1) -> None:
+    _check(load().dil_set_tuning(ctx, op, warps_per_cta, warps_per_task), "dil_set_tuning")
 
 
 def dil_keygen(ctx, level, n, seeds, pk, sk, stream=None):
@@ -219,6 +227,31 @@ def dil_test_issue_rate(ctx, op: int) -> float:
 ISSUE_OPS = {"lop3": 0, "shf": 1, "imul": 2, "imul_hi": 3, "shfl": 4}
 
 
+class SignJob(ctypes.Structure):
+    """dil_sign_job: one batch of Sign tasks of one level (device pointers)."""
+    _fields_ = [("level", ctypes.c_int), ("n", ctypes.c_size_t), ("sk", ctypes.c_void_p),
+                ("msg", ctypes.c_void_p), ("msg_off", ctypes.c_void_p), ("sig", ctypes.c_void_p),
+                ("task_status", ctypes.c_void_p), ("iterations", ctypes.c_void_p)]
+
+
+def sign_job(level, n, sk, msg, msg_off, sig, task_status=None, iterations=None) -> SignJob:
+    return SignJob(level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(task_status), _ptr(iterations))
+
+
+def dil_sign_persistent(ctx, jobs, stream=None):
+    arr = (SignJob * len(jobs))(*jobs)
+    return _check(load().dil_sign_persistent(ctx, len(jobs), arr, _stream(stream)), "dil_sign_persistent")
+
+
+def dil_set_persistent_tuning(ctx, warps_per_cta=8, warps_per_task=2, ctas_per_sm=0, chunk=1, speculation=4):
+    return _check(load().dil_set_persistent_tuning(ctx, warps_per_cta, warps_per_task, ctas_per_sm, chunk,
+                                                   speculation), "dil_set_persistent_tuning")
+
+
+def dil_persistent_status(ctx, stream=None) -> int:
+    return load().dil_persistent_status(ctx, _stream(stream))
+
+
 # ----------------------------------------------------------------- wrapper
 class Context:
     """Owns a dil_ctx.  Methods take and return torch CUDA tensors."""
@@ -243,6 +276,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_tuning(self, op: int, warps_per_cta: int, warps_per_task: int = 1) -> None:
+        dil_set_tuning(self.handle, op, warps_per_cta, warps_per_task)
 
     def set_max_iter(self, max_iter: int) -> None:
         dil_set_max_iter(self.handle, max_iter)

@@ -160,3 +160,30 @@ def test_host_forms_match_device_forms(ctx, orc):
     ok = np.zeros(64, np.uint8)
     dil.dil_verify_host(ctx.handle, level, 64, pk, msg, off, sig, ok)
     assert ok.all()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 2), (4, 2), (4, 4), (8, 4), (8, 1)])
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_launch_shapes_bit_exact(orc, level, shape):
+    """Every launch shape (warps per CTA, warps per task) gives the oracle's
+    bytes: keys, signatures, repetition counts and accept bits."""
+    from gpu_util import gpu_keygen, gpu_sign, gpu_verify
+    from paper_2211_12265_gb300 import dil
+    n = 37                                          # ragged against every group size
+    seeds, msg, off = _batch(orc, level, n, 11 + level, "uniform", 0, 900)
+    opk, osk = orc.keygen_batch(level, seeds)
+    osig, ost, oit = orc.sign_batch(level, osk, msg, off)
+    c = dil.Context(0)
+    try:
+        for op in range(3):
+            c.set_tuning(op, *shape)
+        pk, sk = gpu_keygen(c, level, seeds)
+        sig, st, it = gpu_sign(c, level, osk, msg, off)
+        bad = osig.copy()
+        bad[::3, 40] ^= 1
+        ok = gpu_verify(c, level, opk, msg, off, bad)
+    finally:
+        c.close()
+    assert np.array_equal(pk, opk) and np.array_equal(sk, osk)
+    assert np.array_equal(sig, osig) and np.array_equal(it, oit) and np.array_equal(st, ost)
+    assert np.array_equal(ok, orc.verify_batch(level, opk, msg, off, bad))
