@@ -148,6 +148,86 @@ int dil_set_persistent_tuning(dil_ctx *ctx, int warps_per_cta, int warps_per_tas
  * device-side wait of the last persistent launch on this context ran out. */
 int dil_persistent_status(dil_ctx *ctx, void *stream);
 
+/* ----------------------------------------------------------------------------
+ * Resident keys (for serving many messages per key): a key store keeps, per
+ * key, pk, sk (optional), tr = H(pk) and the key's precomputation (A^ =
+ * ExpandA(rho), NTT(s1), NTT(s2), NTT(t0), NTT(t1 2^d)) on the device, so a
+ * keyed Sign hashes only mu and rho' per message before its loop (Alg 2
+ * l.1-2) and a keyed Verify skips ExpandA and H(pk) (Alg 3 l.1-2).  Outputs
+ * equal dil_sign / dil_verify on the same keys and messages.
+ * ------------------------------------------------------------------------- */
+typedef struct dil_keystore dil_keystore;
+
+/* Copies n_keys public keys (and secret keys, or NULL for a verify-only
+ * store; device pointers) into a new store on ctx's device and enqueues their
+ * precomputation on `stream`.  The store owns its device memory
+ * (n_keys x (pk + sk + 32 + 4 KB (k l + l + 3k)) bytes). */
+int dil_keystore_create(dil_ctx *ctx, int level, size_t n_keys, const uint8_t *pk, const uint8_t *sk,
+                        dil_keystore **out, void *stream);
+/* Frees the store (synchronises its device).  NULL is accepted. */
+int dil_keystore_destroy(dil_keystore *ks);
+/* Sign of n messages, task i with resident key key_idx[i] (device int32).
+ * Needs a store created with secret keys.  A key index outside the store
+ * gives task status DIL_EINVAL and a zero signature. */
+int dil_sign_keyed(dil_ctx *ctx, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
+                   const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream);
+/* Verify of n signatures against resident public keys key_idx[i]; a key index
+ * outside the store gives ok = 0. */
+int dil_verify_keyed(dil_ctx *ctx, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
+                     const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream);
+
+/* ----------------------------------------------------------------------------
+ * Serving loop (continuous batching).  A server owns resident key stores (one
+ * per level), S CUDA streams ("slots") with device and pinned host buffers
+ * sized from a memory budget, and a dispatcher thread.  Whenever a slot is
+ * free and requests are pending, the dispatcher takes them in arrival order
+ * (at most max_batch requests and the slot's message capacity), groups them
+ * by operation and level, and runs the keyed kernels on that slot's stream,
+ * so requests arriving while others run join the next free slot and batches
+ * overlap on the device.  Results equal dil_sign / dil_verify's.  Latency is
+ * measured from a request's arrival to the moment its result is visible to
+ * the host.  All pointers of the server calls are HOST pointers.
+ * ------------------------------------------------------------------------- */
+typedef struct dil_server dil_server;
+
+typedef struct {
+    uint64_t id;
+    int32_t op;          /* 0 = sign, 1 = verify */
+    int32_t level;
+    int32_t status;      /* sign: DIL_OK, DIL_EITER or DIL_EINVAL (unknown key) */
+    uint8_t ok;          /* verify: 1 = accept */
+    uint8_t sig[4595];   /* sign: the signature (first SIG bytes) */
+    double latency_s;    /* arrival to result visible on the host */
+} dil_result;
+
+/* Creates a server on `device` with `streams` slots (1..16).  The slots'
+ * device buffers must fit memory_budget (0 = 4 GiB, key stores excluded):
+ * max_batch is halved until they do (DIL_ENOMEM if even 1 does not fit). */
+int dil_server_create(int device, size_t memory_budget, int streams, int max_batch, dil_server **out);
+/* Stops the dispatcher after in-flight work, frees everything.  NULL accepted. */
+int dil_server_destroy(dil_server *srv);
+/* The admission limits chosen at creation. */
+int dil_server_limits(const dil_server *srv, int *max_batch, size_t *msg_capacity);
+/* Installs n resident key pairs of one level (key ids 0..n-1), replacing the
+ * level's previous store; only while no request is outstanding.  Synchronous. */
+int dil_server_add_keys(dil_server *srv, int level, size_t n, const uint8_t *pk, const uint8_t *sk);
+/* Queues one request (op 0 = sign with key `key`, 1 = verify of `sig` under
+ * key `key`); the message (and signature) are copied.  *id identifies it. */
+int dil_server_submit(dil_server *srv, int op, int level, int32_t key, const uint8_t *msg, size_t mlen,
+                      const uint8_t *sig, uint64_t *id);
+/* Returns up to max_n completed submitted requests (waiting up to wait_us for
+ * the first one); *n_out receives the count. */
+int dil_server_poll(dil_server *srv, dil_result *out, size_t max_n, size_t *n_out, int wait_us);
+/* Open-loop load: request i arrives arrival_s[i] seconds after the call
+ * starts (non-decreasing) and is submitted then; returns when all n are done.
+ * Signatures in/out use a stride of 4595 bytes; msg/msg_off as for dil_sign.
+ * latency_s[i] receives request i's latency, *wall_s the elapsed time. */
+int dil_server_replay(dil_server *srv, size_t n, const double *arrival_s, const int32_t *op, const int32_t *level,
+                      const int32_t *key, const uint8_t *msg, const uint64_t *msg_off, const uint8_t *sig_in,
+                      uint8_t *sig_out, int32_t *status, uint8_t *ok, double *latency_s, double *wall_s);
+/* Batches dispatched and requests they carried since creation. */
+int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests);
+
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
  * msg_off too).  They copy inputs to the device, run on `stream`, copy the
  * results back and synchronise the stream before returning. */

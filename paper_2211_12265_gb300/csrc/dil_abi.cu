@@ -346,6 +346,110 @@ int dil_persistent_status(dil_ctx *c, void *stream) {
     return dil::persist_error(c->pws);
 }
 
+// ---------------------------------------------------------------- key stores
+}  // extern "C"
+
+extern "C" {
+
+int dil_keystore_create(dil_ctx *c, int level, size_t n_keys, const uint8_t *pk, const uint8_t *sk,
+                        dil_keystore **out, void *stream) {
+    if (!c || !out || !level_ok(level) || n_keys == 0 || !pk || n_keys > (size_t)INT32_MAX) return DIL_EINVAL;
+    *out = nullptr;
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    DeviceGuard g(c->device);
+    dil_keystore *ks = new dil_keystore;
+    ks->device = c->device;
+    ks->level = level;
+    ks->n = n_keys;
+    const size_t kbytes = n_keys * dil::key_polys(level) * POLY_BYTES;
+    bool okm = cudaMalloc(&ks->pk, pkb * n_keys) == cudaSuccess && cudaMalloc(&ks->tr, 32 * n_keys) == cudaSuccess &&
+               cudaMalloc(&ks->keys, kbytes) == cudaSuccess;
+    if (okm && sk) okm = cudaMalloc(&ks->sk, skb * n_keys) == cudaSuccess;
+    if (!okm) {
+        cudaGetLastError();
+        dil_keystore_destroy(ks);
+        return DIL_ENOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ks->pk, pk, pkb * n_keys, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && sk) e = cudaMemcpyAsync(ks->sk, sk, skb * n_keys, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = dil::launch_key_prepare(level, (int)n_keys, ks->pk, ks->sk, ks->keys, ks->tr, 8, 2, s);
+    if (e != cudaSuccess) {
+        dil_keystore_destroy(ks);
+        return cuda_fail(e);
+    }
+    *out = ks;
+    return DIL_OK;
+}
+
+int dil_keystore_destroy(dil_keystore *ks) {
+    if (!ks) return DIL_OK;
+    {
+        DeviceGuard g(ks->device);
+        cudaDeviceSynchronize();
+        if (ks->pk) cudaFree(ks->pk);
+        if (ks->sk) cudaFree(ks->sk);
+        if (ks->tr) cudaFree(ks->tr);
+        if (ks->keys) cudaFree(ks->keys);
+    }
+    delete ks;
+    return DIL_OK;
+}
+
+int dil_sign_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
+                   const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream) {
+    if (!c || !ks || !ks->sk || ks->device != c->device) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!key_idx || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(ks->level, pkb, skb, sigb);
+    const int l = ks->level == 2 ? 4 : ks->level == 3 ? 5 : 7;
+    const int cap = (65536 - l) / l + 1;
+    const int max_iter = (c->max_iter > 0 && c->max_iter < cap) ? c->max_iter : cap;
+    const size_t per = dil::keyed_sign_polys(ks->level) * POLY_BYTES;
+    size_t chunk = std::min<size_t>(n, c->budget / per);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * per);
+    if (rc) return rc;
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_sign_keyed(ks->level, m, (int)ks->n, key_idx + s0, ks->sk, ks->keys, msg,
+                                               msg_off + s0, sig + sigb * s0,
+                                               task_status ? task_status + s0 : nullptr, nullptr, (int32_t *)c->ws,
+                                               max_iter, c->warps[1], c->wpt[1], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
+int dil_verify_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
+                     const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream) {
+    if (!c || !ks || ks->device != c->device) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!key_idx || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(ks->level, pkb, skb, sigb);
+    const size_t per = dil::scratch_polys(dil::OP_VERIFY, ks->level) * POLY_BYTES;
+    size_t chunk = std::min<size_t>(n, c->budget / per);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * per);
+    if (rc) return rc;
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_verify_keyed(ks->level, m, (int)ks->n, key_idx + s0, ks->pk, ks->keys, ks->tr,
+                                                 msg, msg_off + s0, sig + sigb * s0, ok + s0, (int32_t *)c->ws,
+                                                 c->warps[2], c->wpt[2], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
 // ---------------------------------------------------------------- host forms
 namespace {
 

@@ -6,6 +6,16 @@
 
 #include <cuda_runtime.h>
 
+// A resident key store (see dil_keystore_create): device copies of the keys,
+// tr = H(pk) and each key's precomputation (KEY_POLYS polynomials).
+struct dil_keystore {
+    int device = 0;
+    int level = 0;
+    size_t n = 0;
+    uint8_t *pk = nullptr, *sk = nullptr, *tr = nullptr;
+    int32_t *keys = nullptr;
+};
+
 namespace dil {
 
 enum Op { OP_KEYGEN = 0, OP_SIGN = 1, OP_VERIFY = 2 };
@@ -23,6 +33,21 @@ cudaError_t launch_sign(int level, int n, const uint8_t *sk, const uint8_t *msg,
                         int warps, int p, cudaStream_t s);
 cudaError_t launch_verify(int level, int n, const uint8_t *pk, const uint8_t *msg, const uint64_t *off,
                           const uint8_t *sig, uint8_t *ok, int32_t *scratch, int warps, int p, cudaStream_t s);
+
+// resident keys: per-key polynomials (A^, s^1, s^2, t^0, NTT(t1 2^d)) and
+// per-task scratch of a keyed Sign (y, y^, w, z)
+size_t key_polys(int level);
+size_t keyed_sign_polys(int level);
+cudaError_t launch_key_prepare(int level, int n, const uint8_t *pk, const uint8_t *sk, int32_t *keys, uint8_t *tr,
+                               int warps, int p, cudaStream_t s);
+// key indices outside [0, n_keys) are rejected per task (status DIL_EINVAL / ok 0)
+cudaError_t launch_sign_keyed(int level, int n, int n_keys, const int32_t *key_idx, const uint8_t *sk,
+                              const int32_t *keys, const uint8_t *msg, const uint64_t *off, uint8_t *sig,
+                              int32_t *status, int32_t *iters, int32_t *scratch, int max_iter, int warps, int p,
+                              cudaStream_t s);
+cudaError_t launch_verify_keyed(int level, int n, int n_keys, const int32_t *key_idx, const uint8_t *pk,
+                                const int32_t *keys, const uint8_t *tr, const uint8_t *msg, const uint64_t *off,
+                                const uint8_t *sig, uint8_t *ok, int32_t *scratch, int warps, int p, cudaStream_t s);
 
 // primitives (test-only entry points)
 cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t *off, uint8_t *out,

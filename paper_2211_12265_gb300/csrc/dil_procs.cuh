@@ -142,6 +142,9 @@ template <int LEVEL> struct Scratch {
     static constexpr int SIGN_POLYS = PRE_POLYS + ITR_POLYS;
     static constexpr int GEN_POLYS = V::L;     // s^1
     static constexpr int VERIFY_POLYS = V::L;  // z^
+    // resident key: the Sign precomputation followed by NTT(t1 2^d)
+    static constexpr int T1H = PRE_POLYS;
+    static constexpr int KEY_POLYS = T1H + V::K;
 };
 
 // acc = sum_j A^_ij o v^_j (pointwise Montgomery products) for one row i of A^,
@@ -330,6 +333,81 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
     group_sync<P>(bar);
 }
 
+// Per-message precomputation of a Sign with a resident key (A^, s^1, s^2, t^0
+// already prepared): mu = H(tr || M) and rho' = H(K || mu) on warp 0.
+template <int LEVEL, int P>
+__device__ void sign_prepare_keyed(const uint8_t *__restrict__ sk, const uint8_t *__restrict__ msg, size_t mlen,
+                                   GroupSmem &gs, int g, int bar, int lane) {
+    if (g == 0) {
+        gs.hb[HB_K + lane] = __ldg(sk + 32 + lane);
+        gs.tr[lane] = __ldg(sk + 64 + lane);
+        __syncwarp();
+        uint32_t lo = 0, hi = 0;
+        absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
+        squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        __syncwarp();
+        lo = 0;
+        hi = 0;
+        absorb_smem(lo, hi, gs.hb + HB_K, 96, 136, lane);
+        squeeze_words(lo, hi, gs.rhop, 8, lane);
+    }
+    group_sync<P>(bar);
+}
+
+// Prepares one resident key: A^ = ExpandA(rho), s^1, s^2, t^0 (from sk, when
+// given) and NTT(t1 2^d) into `key` (KEY_POLYS polynomials), tr = H(pk).
+template <int LEVEL, int P>
+__device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__restrict__ sk, int32_t *key,
+                            uint8_t *tr_out, GroupSmem &gs, WarpSmem &ws, const int32_t *zt, int g, int bar,
+                            int lane) {
+    using V = Lv<LEVEL>;
+    using S = Scratch<LEVEL>;
+    int32_t r[8];
+    if (g == 0) gs.rho[lane] = __ldg(pk + lane);
+    group_sync<P>(bar);
+    constexpr int KL = V::K * V::L;
+    constexpr int UA = Units<KL, P>::SIZE;
+    for (int p = UA * g; p < KL; p += UA * P) {
+        int32_t a[8];
+        if (UA == 2) {
+            expand_a_pair(gs.rho, p / V::L, p % V::L, (p + 1) / V::L, (p + 1) % V::L, ws.buf, ws.buf2, ws.sq,
+                          ws.sq2, lane);
+            read_buf_l2(a, ws.buf2, lane);
+            store_l2(key + (S::AH + p + 1) * N, a, lane);
+        } else {
+            expand_a_poly(gs.rho, p / V::L, p % V::L, ws.buf, ws.sq, lane);
+        }
+        read_buf_l2(a, ws.buf, lane);
+        store_l2(key + (S::AH + p) * N, a, lane);
+        __syncwarp();
+    }
+    // s^1, s^2, t^0 (when the secret key is resident) and NTT(t1 2^d)
+    const int first = sk ? 0 : V::L + 2 * V::K;
+    for (int u = first + g; u < V::L + 3 * V::K; u += P) {
+        if (u < V::L) {
+            unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S1 + u * V::POLYETA, V::ETA, ws, lane);
+        } else if (u < V::L + V::K) {
+            unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S2 + (u - V::L) * V::POLYETA, V::ETA, ws, lane);
+        } else if (u < V::L + 2 * V::K) {
+            unpack_poly_l0<D>(r, sk + V::SK_T0 + (u - V::L - V::K) * V::POLYT0, 1 << (D - 1), ws, lane);
+        } else {
+            unpack_poly_l0<10>(r, pk + 32 + (u - V::L - 2 * V::K) * V::POLYT1, 0, ws, lane);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) r[m] = (-r[m]) << D;   // t1 2^d
+        }
+        ntt_fwd(r, ws.buf, zt, lane);
+        store_l2(key + (S::S1H + u) * N, r, lane);   // S1H, S2H, T0H, T1H are contiguous
+    }
+    if (g == P - 1) {
+        uint32_t lo = 0, hi = 0;
+        absorb_concat(lo, hi, gs.tr, 0, pk, V::PK, 136, lane);
+        squeeze_words(lo, hi, gs.tr, 4, lane);
+        __syncwarp();
+        tr_out[lane] = gs.tr[lane];
+    }
+    group_sync<P>(bar);
+}
+
 // One repetition of the rejection loop with nonce base kappa (l.6-18), with
 // early evaluation: each polynomial is checked as soon as it is produced.
 // Returns true (on every warp of the group) when (z, h) is accepted; then
@@ -510,10 +588,13 @@ __device__ void sign_zero(uint8_t *sig, int g, int lane) {
 // Alg 3: Verify.  Returns 1 (accept) or 0 on every warp of the group.
 // scratch: VERIFY_POLYS polys.
 // -------------------------------------------------------------------------
-template <int LEVEL, int P>
+// KEYED: the public key is resident; `key` holds its A^ and NTT(t1 2^d)
+// (KEY_POLYS layout) and `tr` its H(pk), so neither is recomputed.
+template <int LEVEL, int P, bool KEYED = false>
 __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__restrict__ msg, size_t mlen,
                            const uint8_t *__restrict__ sig, int32_t *scratch, GroupSmem &gs, WarpSmem &ws,
-                           const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
+                           const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
+                           const int32_t *key = nullptr, const uint8_t *tr = nullptr) {
     using V = Lv<LEVEL>;
     volatile int *vflag = &gs.flag;
     int32_t r[8], acc[8], ch[8];
@@ -564,8 +645,12 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     // mu = H(H(rho || t1) || M)  (l.2), on the last warp
     if (g == P - 1) {
         uint32_t lo = 0, hi = 0;
-        absorb_concat(lo, hi, gs.tr, 0, pk, V::PK, 136, lane);
-        squeeze_words(lo, hi, gs.tr, 4, lane);
+        if (KEYED) {
+            gs.tr[lane] = __ldcg(tr + lane);
+        } else {
+            absorb_concat(lo, hi, gs.tr, 0, pk, V::PK, 136, lane);
+            squeeze_words(lo, hi, gs.tr, 4, lane);
+        }
         __syncwarp();
         lo = 0;
         hi = 0;
@@ -578,11 +663,25 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)  (l.4-5)
     for (int i = g; i < V::K; i += P) {
-        accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
-        unpack_poly_l0<10>(r, pk + 32 + i * V::POLYT1, 0, ws, lane);
+        if (KEYED) {
+            using S = Scratch<LEVEL>;
+            int32_t a[8], zv[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) r[m] = (-r[m]) << D;   // t1 2^d, t1 stored as 0 - field
-        ntt_fwd(r, ws.buf, zt, lane);
+            for (int m = 0; m < 8; ++m) acc[m] = 0;
+            for (int j = 0; j < V::L; ++j) {
+                load_l2_cg(a, key + (S::AH + i * V::L + j) * N, lane);
+                load_l2(zv, scratch + j * N, lane);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], zv[m]);
+            }
+            load_l2_cg(r, key + (S::T1H + i) * N, lane);
+        } else {
+            accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
+            unpack_poly_l0<10>(r, pk + 32 + i * V::POLYT1, 0, ws, lane);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) r[m] = (-r[m]) << D;   // t1 2^d, t1 stored as 0 - field
+            ntt_fwd(r, ws.buf, zt, lane);
+        }
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = reduce_q(acc[m] - mont_mul(ch[m], r[m]));
         ntt_inv(acc, ws.buf, izt, lane);

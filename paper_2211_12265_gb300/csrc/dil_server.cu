@@ -1,0 +1,492 @@
+// Serving loop: continuous batching of mixed Sign / Verify requests of any
+// level and message length over resident keys.
+//
+// A dispatcher thread owns S stream slots.  Whenever a slot is free and
+// requests are pending it takes them in arrival order, as many as the slot's
+// admission limits allow (max_batch requests, msg_capacity message bytes; the
+// slot's device buffers are sized once from the memory budget), groups them by
+// (operation, level), copies their inputs through pinned buffers, launches
+// the keyed kernels on the slot's stream and copies the results back.  New
+// requests therefore join as soon as any slot frees up, and batches on
+// different slots run concurrently on the device.  A request's latency runs
+// from its arrival to the moment its result is visible to the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/dil.h"
+#include "dil_launch.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+constexpr int MAX_SIG = 4595;
+constexpr size_t POLY = 256 * sizeof(int32_t);
+constexpr size_t MAX_TASK_POLYS = 29;   // keyed Sign scratch of level 5 (largest of all keyed tasks)
+
+int level_slot(int level) { return level == 2 ? 0 : level == 3 ? 1 : level == 5 ? 2 : -1; }
+size_t sig_bytes(int level) { return level == 2 ? 2420 : level == 3 ? 3293 : 4595; }
+
+struct Req {
+    uint64_t id = 0;
+    int op = 0, level = 2;
+    int32_t key = 0;
+    const uint8_t *msg = nullptr;
+    size_t mlen = 0;
+    const uint8_t *sig_in = nullptr;
+    double t_arrive = 0;
+    // result destinations
+    uint8_t *sig_out = nullptr;
+    int32_t *status = nullptr;
+    uint8_t *ok = nullptr;
+    double *latency = nullptr;
+    // owned storage (submit / poll mode)
+    std::vector<uint8_t> own_msg, own_sig_in;
+    dil_result res;
+    bool owned = false;
+};
+
+struct Group {
+    int op, level, first, count;
+    size_t off_first;   // index of the group's first offset in the offset array
+    size_t sig_first;   // byte offset of the group's signatures
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    uint8_t *d_msg = nullptr, *d_sig_in = nullptr, *d_sig_out = nullptr, *d_ok = nullptr;
+    uint64_t *d_off = nullptr;
+    int32_t *d_key = nullptr, *d_status = nullptr, *d_scratch = nullptr;
+    uint8_t *h_msg = nullptr, *h_sig_in = nullptr, *h_sig_out = nullptr, *h_ok = nullptr;
+    uint64_t *h_off = nullptr;
+    int32_t *h_key = nullptr, *h_status = nullptr;
+    std::vector<Req *> reqs;
+    std::vector<Group> groups;
+    size_t sig_used = 0;
+};
+
+}  // namespace
+
+struct dil_server {
+    int device = 0;
+    int max_batch = 0;
+    size_t msg_cap = 0;
+    dil_ctx *ctx = nullptr;
+    dil_keystore *ks[3] = {nullptr, nullptr, nullptr};
+    int nkeys[3] = {0, 0, 0};
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> pending;
+    std::deque<Req *> completed;
+    size_t outstanding = 0;   // submitted and not yet completed
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_id = 1;
+    uint64_t batches = 0, batched_reqs = 0;
+};
+
+namespace {
+
+void free_slot(Slot &s) {
+    cudaFree(s.d_msg); cudaFree(s.d_sig_in); cudaFree(s.d_sig_out); cudaFree(s.d_ok);
+    cudaFree(s.d_off); cudaFree(s.d_key); cudaFree(s.d_status); cudaFree(s.d_scratch);
+    cudaFreeHost(s.h_msg); cudaFreeHost(s.h_sig_in); cudaFreeHost(s.h_sig_out); cudaFreeHost(s.h_ok);
+    cudaFreeHost(s.h_off); cudaFreeHost(s.h_key); cudaFreeHost(s.h_status);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot();
+}
+
+bool alloc_slot(Slot &s, int max_batch, size_t msg_cap) {
+    const size_t n = (size_t)max_batch, offs = n + 6;
+    bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&s.d_msg, msg_cap + 16) == cudaSuccess &&
+              cudaMalloc(&s.d_sig_in, n * MAX_SIG) == cudaSuccess &&
+              cudaMalloc(&s.d_sig_out, n * MAX_SIG) == cudaSuccess && cudaMalloc(&s.d_ok, n) == cudaSuccess &&
+              cudaMalloc(&s.d_off, offs * 8) == cudaSuccess && cudaMalloc(&s.d_key, n * 4) == cudaSuccess &&
+              cudaMalloc(&s.d_status, n * 4) == cudaSuccess &&
+              cudaMalloc(&s.d_scratch, n * MAX_TASK_POLYS * POLY) == cudaSuccess &&
+              cudaMallocHost(&s.h_msg, msg_cap + 16) == cudaSuccess &&
+              cudaMallocHost(&s.h_sig_in, n * MAX_SIG) == cudaSuccess &&
+              cudaMallocHost(&s.h_sig_out, n * MAX_SIG) == cudaSuccess && cudaMallocHost(&s.h_ok, n) == cudaSuccess &&
+              cudaMallocHost(&s.h_off, offs * 8) == cudaSuccess && cudaMallocHost(&s.h_key, n * 4) == cudaSuccess &&
+              cudaMallocHost(&s.h_status, n * 4) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+size_t slot_device_bytes(int max_batch, size_t msg_cap) {
+    const size_t n = (size_t)max_batch;
+    return msg_cap + 16 + 2 * n * MAX_SIG + n + (n + 6) * 8 + 8 * n + n * MAX_TASK_POLYS * POLY;
+}
+
+void finish_request(dil_server *sv, Req *r, double t) {
+    if (r->latency) *r->latency = t - r->t_arrive;
+    r->res.latency_s = t - r->t_arrive;
+}
+
+// Starts the next batch on a free slot; returns false when nothing was pending.
+bool dispatch(dil_server *sv, Slot &s) {
+    s.reqs.clear();
+    s.groups.clear();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        size_t bytes = 0;
+        while (!sv->pending.empty() && (int)s.reqs.size() < sv->max_batch) {
+            Req *r = sv->pending.front();
+            if (bytes + r->mlen > sv->msg_cap && !s.reqs.empty()) break;   // waits for the next batch
+            sv->pending.pop_front();
+            bytes += r->mlen;
+            s.reqs.push_back(r);
+        }
+    }
+    if (s.reqs.empty()) return false;
+    // group by (op, level), stable within a group
+    std::stable_sort(s.reqs.begin(), s.reqs.end(), [](const Req *a, const Req *b) {
+        return a->op != b->op ? a->op < b->op : a->level < b->level;
+    });
+    size_t mbytes = 0, noff = 0, sig_off = 0;
+    for (int i = 0; i < (int)s.reqs.size();) {
+        Group g{s.reqs[i]->op, s.reqs[i]->level, i, 0, noff, sig_off};
+        int j = i;
+        while (j < (int)s.reqs.size() && s.reqs[j]->op == g.op && s.reqs[j]->level == g.level) {
+            Req *r = s.reqs[j];
+            const size_t sb = sig_bytes(r->level);
+            s.h_key[j] = r->key;
+            s.h_off[noff++] = mbytes;
+            if (r->mlen) memcpy(s.h_msg + mbytes, r->msg, std::min(r->mlen, sv->msg_cap - mbytes));
+            mbytes += std::min(r->mlen, sv->msg_cap - mbytes);
+            if (g.op == 1) memcpy(s.h_sig_in + sig_off, r->sig_in, sb);
+            sig_off += sb;
+            ++j;
+        }
+        s.h_off[noff++] = mbytes;
+        g.count = j - i;
+        s.groups.push_back(g);
+        i = j;
+    }
+    s.sig_used = sig_off;
+    const size_t n = s.reqs.size();
+    cudaStream_t st = s.stream;
+    cudaMemcpyAsync(s.d_key, s.h_key, n * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s.d_off, s.h_off, noff * 8, cudaMemcpyHostToDevice, st);
+    if (mbytes) cudaMemcpyAsync(s.d_msg, s.h_msg, mbytes, cudaMemcpyHostToDevice, st);
+    bool any_verify = false;
+    for (auto &g : s.groups) any_verify |= g.op == 1;
+    if (any_verify) cudaMemcpyAsync(s.d_sig_in, s.h_sig_in, sig_off, cudaMemcpyHostToDevice, st);
+    for (auto &g : s.groups) {
+        const int li = level_slot(g.level);
+        dil_keystore *ks = sv->ks[li];
+        int32_t *scratch = s.d_scratch + (size_t)g.first * MAX_TASK_POLYS * 256;
+        if (g.op == 0) {
+            const int l = g.level == 2 ? 4 : g.level == 3 ? 5 : 7;
+            dil::launch_sign_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->sk, ks->keys, s.d_msg,
+                                   s.d_off + g.off_first, s.d_sig_out + g.sig_first, s.d_status + g.first, nullptr,
+                                   scratch, (65536 - l) / l + 1, 8, 2, st);
+        } else {
+            dil::launch_verify_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->pk, ks->keys, ks->tr,
+                                     s.d_msg, s.d_off + g.off_first, s.d_sig_in + g.sig_first, s.d_ok + g.first,
+                                     scratch, 8, 2, st);
+        }
+    }
+    cudaMemcpyAsync(s.h_sig_out, s.d_sig_out, sig_off, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(s.h_status, s.d_status, n * 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(s.h_ok, s.d_ok, n, cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(s.done, st);
+    s.busy = true;
+    sv->batches++;
+    sv->batched_reqs += n;
+    return true;
+}
+
+void complete(dil_server *sv, Slot &s) {
+    const double t = now_s();
+    for (auto &g : s.groups) {
+        size_t so = g.sig_first;
+        for (int i = g.first; i < g.first + g.count; ++i) {
+            Req *r = s.reqs[i];
+            const size_t sb = sig_bytes(r->level);
+            r->res.status = 0;
+            r->res.ok = 0;
+            if (g.op == 0) {
+                r->res.status = s.h_status[i];
+                if (r->status) *r->status = s.h_status[i];
+                if (r->sig_out) memcpy(r->sig_out, s.h_sig_out + so, sb);
+                if (r->owned) memcpy(r->res.sig, s.h_sig_out + so, sb);
+            } else {
+                r->res.ok = s.h_ok[i];
+                if (r->ok) *r->ok = s.h_ok[i];
+            }
+            so += sb;
+            finish_request(sv, r, t);
+        }
+    }
+    s.busy = false;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (Req *r : s.reqs) {
+        if (r->owned)
+            sv->completed.push_back(r);
+        else
+            delete r;
+        sv->outstanding--;
+    }
+    s.reqs.clear();
+    sv->cv_done.notify_all();
+}
+
+void worker_loop(dil_server *sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        bool progressed = false;
+        for (auto &s : sv->slots) {
+            if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
+                complete(sv, s);
+                progressed = true;
+            }
+        }
+        for (auto &s : sv->slots)
+            if (!s.busy && dispatch(sv, s)) progressed = true;
+        bool any_busy = false;
+        for (auto &s : sv->slots) any_busy |= s.busy;
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (sv->stop && !any_busy && sv->pending.empty()) return;
+        if (!progressed) {
+            if (any_busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(10));
+            } else {
+                sv->cv_work.wait_for(lk, std::chrono::milliseconds(5),
+                                     [&] { return sv->stop || !sv->pending.empty(); });
+            }
+        }
+    }
+}
+
+void enqueue(dil_server *sv, std::vector<Req *> &batch) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (Req *r : batch) sv->pending.push_back(r);
+    sv->outstanding += batch.size();
+    batch.clear();
+    sv->cv_work.notify_one();
+}
+
+}  // namespace
+
+extern "C" {
+
+int dil_server_create(int device, size_t memory_budget, int streams, int max_batch, dil_server **out) {
+    if (!out || streams < 1 || streams > 16 || max_batch < 1) return DIL_EINVAL;
+    *out = nullptr;
+    dil_server *sv = new dil_server;
+    sv->device = device;
+    int rc = dil_ctx_create(device, 0, &sv->ctx);
+    if (rc) {
+        delete sv;
+        return rc;
+    }
+    cudaSetDevice(device);
+    const size_t budget = memory_budget ? memory_budget : ((size_t)4 << 30);
+    // admission limits from the budget: shrink the batch until S slots fit
+    size_t msg_cap = (size_t)max_batch * 4096;
+    while (max_batch > 1 && (size_t)streams * slot_device_bytes(max_batch, msg_cap) > budget) {
+        max_batch /= 2;
+        msg_cap = (size_t)max_batch * 4096;
+    }
+    if ((size_t)streams * slot_device_bytes(max_batch, msg_cap) > budget) {
+        dil_ctx_destroy(sv->ctx);
+        delete sv;
+        return DIL_ENOMEM;
+    }
+    if (msg_cap < 16384) msg_cap = 16384;   // any single message fits a batch of its own
+    sv->max_batch = max_batch;
+    sv->msg_cap = msg_cap;
+    sv->slots.resize(streams);
+    for (auto &s : sv->slots) {
+        if (!alloc_slot(s, max_batch, msg_cap)) {
+            for (auto &t : sv->slots) free_slot(t);
+            dil_ctx_destroy(sv->ctx);
+            delete sv;
+            return DIL_ENOMEM;
+        }
+    }
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return DIL_OK;
+}
+
+int dil_server_destroy(dil_server *sv) {
+    if (!sv) return DIL_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->cv_work.notify_all();
+    }
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    cudaDeviceSynchronize();
+    for (auto &s : sv->slots) free_slot(s);
+    for (auto &r : sv->completed) delete r;
+    for (int i = 0; i < 3; ++i) dil_keystore_destroy(sv->ks[i]);
+    dil_ctx_destroy(sv->ctx);
+    delete sv;
+    return DIL_OK;
+}
+
+int dil_server_limits(const dil_server *sv, int *max_batch, size_t *msg_capacity) {
+    if (!sv) return DIL_EINVAL;
+    if (max_batch) *max_batch = sv->max_batch;
+    if (msg_capacity) *msg_capacity = sv->msg_cap;
+    return DIL_OK;
+}
+
+int dil_server_add_keys(dil_server *sv, int level, size_t n, const uint8_t *pk, const uint8_t *sk) {
+    const int li = level_slot(level);
+    if (!sv || li < 0 || n == 0 || n > (size_t)INT32_MAX || !pk || !sk) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->outstanding) return DIL_EINVAL;   // keys change only while idle
+    size_t pkb, skb, sigb;
+    dil_sizes(level, &pkb, &skb, &sigb);
+    cudaSetDevice(sv->device);
+    uint8_t *dpk = nullptr, *dsk = nullptr;
+    if (cudaMalloc(&dpk, pkb * n) != cudaSuccess || cudaMalloc(&dsk, skb * n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dpk);
+        return DIL_ENOMEM;
+    }
+    int rc = DIL_OK;
+    if (cudaMemcpy(dpk, pk, pkb * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dsk, sk, skb * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = DIL_ECUDA;
+    dil_keystore *ks = nullptr;
+    if (!rc) rc = dil_keystore_create(sv->ctx, level, n, dpk, dsk, &ks, nullptr);
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = DIL_ECUDA;
+    cudaFree(dpk);
+    cudaFree(dsk);
+    if (rc) {
+        dil_keystore_destroy(ks);
+        return rc;
+    }
+    dil_keystore_destroy(sv->ks[li]);
+    sv->ks[li] = ks;
+    sv->nkeys[li] = (int)n;
+    return DIL_OK;
+}
+
+int dil_server_submit(dil_server *sv, int op, int level, int32_t key, const uint8_t *msg, size_t mlen,
+                      const uint8_t *sig, uint64_t *id) {
+    const int li = level_slot(level);
+    if (!sv || li < 0 || (op != 0 && op != 1) || !sv->ks[li] || (mlen && !msg) || (op == 1 && !sig)) return DIL_EINVAL;
+    if (mlen > sv->msg_cap) return DIL_EINVAL;
+    Req *r = new Req;
+    r->owned = true;
+    r->op = op;
+    r->level = level;
+    r->key = key;
+    r->own_msg.assign(msg, msg + mlen);
+    r->msg = r->own_msg.data();
+    r->mlen = mlen;
+    if (op == 1) {
+        r->own_sig_in.assign(sig, sig + sig_bytes(level));
+        r->sig_in = r->own_sig_in.data();
+    }
+    memset(&r->res, 0, sizeof(r->res));
+    r->t_arrive = now_s();
+    std::vector<Req *> b{r};
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->id = sv->next_id++;
+        r->res.id = r->id;
+        r->res.op = op;
+        r->res.level = level;
+    }
+    if (id) *id = r->id;
+    enqueue(sv, b);
+    return DIL_OK;
+}
+
+int dil_server_poll(dil_server *sv, dil_result *out, size_t max_n, size_t *n_out, int wait_us) {
+    if (!sv || !out || !n_out) return DIL_EINVAL;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (sv->completed.empty() && wait_us > 0)
+        sv->cv_done.wait_for(lk, std::chrono::microseconds(wait_us), [&] { return !sv->completed.empty(); });
+    size_t k = 0;
+    while (k < max_n && !sv->completed.empty()) {
+        Req *r = sv->completed.front();
+        sv->completed.pop_front();
+        out[k++] = r->res;
+        delete r;
+    }
+    *n_out = k;
+    return DIL_OK;
+}
+
+int dil_server_replay(dil_server *sv, size_t n, const double *arrival_s, const int32_t *op, const int32_t *level,
+                      const int32_t *key, const uint8_t *msg, const uint64_t *msg_off, const uint8_t *sig_in,
+                      uint8_t *sig_out, int32_t *status, uint8_t *ok, double *latency_s, double *wall_s) {
+    if (!sv || !arrival_s || !op || !level || !key || !msg_off || !latency_s) return DIL_EINVAL;
+    for (size_t i = 0; i < n; ++i) {
+        const int li = level_slot(level[i]);
+        if (li < 0 || !sv->ks[li] || (op[i] != 0 && op[i] != 1)) return DIL_EINVAL;
+        if (op[i] == 1 && !sig_in) return DIL_EINVAL;
+        if (op[i] == 0 && (!sig_out || !status)) return DIL_EINVAL;
+        if (op[i] == 1 && !ok) return DIL_EINVAL;
+        if (msg_off[i + 1] - msg_off[i] > sv->msg_cap) return DIL_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->outstanding) return DIL_EINVAL;
+    }
+    const double t0 = now_s();
+    std::vector<Req *> batch;
+    size_t i = 0;
+    while (i < n) {
+        const double t = now_s() - t0;
+        while (i < n && arrival_s[i] <= t) {
+            Req *r = new Req;
+            r->op = op[i];
+            r->level = level[i];
+            r->key = key[i];
+            r->msg = msg + msg_off[i];
+            r->mlen = (size_t)(msg_off[i + 1] - msg_off[i]);
+            r->sig_in = sig_in ? sig_in + i * MAX_SIG : nullptr;
+            r->sig_out = sig_out ? sig_out + i * MAX_SIG : nullptr;
+            r->status = status ? status + i : nullptr;
+            r->ok = ok ? ok + i : nullptr;
+            r->latency = latency_s + i;
+            r->t_arrive = t0 + arrival_s[i];
+            batch.push_back(r);
+            ++i;
+        }
+        if (!batch.empty()) enqueue(sv, batch);
+        if (i < n) {
+            const double wait = arrival_s[i] - (now_s() - t0);
+            if (wait > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait - 100e-6) * 1e6)));
+        }
+    }
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->cv_done.wait(lk, [&] { return sv->outstanding == 0; });
+    if (wall_s) *wall_s = now_s() - t0;
+    return DIL_OK;
+}
+
+int dil_server_stats(const dil_server *sv, uint64_t *batches, uint64_t *requests) {
+    if (!sv) return DIL_EINVAL;
+    if (batches) *batches = sv->batches;
+    if (requests) *requests = sv->batched_reqs;
+    return DIL_OK;
+}
+
+}  // extern "C"

@@ -71,6 +71,18 @@ def load() -> ctypes.CDLL:
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
                 "dil_persistent_status": [P, P],
+                "dil_keystore_create": [P, I, S, P, P, P, P],
+                "dil_keystore_destroy": [P],
+                "dil_sign_keyed": [P, P, S, P, P, P, P, P, P],
+                "dil_verify_keyed": [P, P, S, P, P, P, P, P, P],
+                "dil_server_create": [I, S, I, I, P],
+                "dil_server_destroy": [P],
+                "dil_server_limits": [P, P, P],
+                "dil_server_add_keys": [P, I, S, P, P],
+                "dil_server_submit": [P, I, I, ctypes.c_int32, P, S, P, P],
+                "dil_server_poll": [P, P, S, P, I],
+                "dil_server_replay": [P, S, P, P, P, P, P, P, P, P, P, P, P, P],
+                "dil_server_stats": [P, P, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -250,6 +262,83 @@ def dil_set_persistent_tuning(ctx, warps_per_cta=8, warps_per_task=2, ctas_per_s
 
 def dil_persistent_status(ctx, stream=None) -> int:
     return load().dil_persistent_status(ctx, _stream(stream))
+
+
+def dil_keystore_create(ctx, level, n_keys, pk, sk=None, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dil_keystore_create(ctx, level, n_keys, _ptr(pk), _ptr(sk), ctypes.byref(h), _stream(stream)),
+           "dil_keystore_create")
+    return h.value
+
+
+def dil_keystore_destroy(ks) -> None:
+    _check(load().dil_keystore_destroy(ks), "dil_keystore_destroy")
+
+
+def dil_sign_keyed(ctx, ks, n, key_idx, msg, msg_off, sig, task_status=None, stream=None):
+    return _check(load().dil_sign_keyed(ctx, ks, n, _ptr(key_idx), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                        _ptr(task_status), _stream(stream)), "dil_sign_keyed")
+
+
+def dil_verify_keyed(ctx, ks, n, key_idx, msg, msg_off, sig, ok, stream=None):
+    return _check(load().dil_verify_keyed(ctx, ks, n, _ptr(key_idx), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(ok),
+                                          _stream(stream)), "dil_verify_keyed")
+
+
+class DilResult(ctypes.Structure):
+    """dil_result: one completed serving request."""
+    _fields_ = [("id", ctypes.c_uint64), ("op", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("ok", ctypes.c_uint8), ("sig", ctypes.c_uint8 * 4595),
+                ("latency_s", ctypes.c_double)]
+
+
+def dil_server_create(device=0, memory_budget=0, streams=4, max_batch=2048) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dil_server_create(device, memory_budget, streams, max_batch, ctypes.byref(h)), "dil_server_create")
+    return h.value
+
+
+def dil_server_destroy(srv) -> None:
+    _check(load().dil_server_destroy(srv), "dil_server_destroy")
+
+
+def dil_server_limits(srv) -> tuple[int, int]:
+    mb, mc = ctypes.c_int(), ctypes.c_size_t()
+    _check(load().dil_server_limits(srv, ctypes.byref(mb), ctypes.byref(mc)), "dil_server_limits")
+    return mb.value, mc.value
+
+
+def dil_server_add_keys(srv, level, n, pk, sk) -> None:
+    _check(load().dil_server_add_keys(srv, level, n, _ptr(pk), _ptr(sk)), "dil_server_add_keys")
+
+
+def dil_server_submit(srv, op, level, key, msg: bytes, sig: bytes | None = None) -> int:
+    rid = ctypes.c_uint64()
+    m = (ctypes.c_uint8 * max(len(msg), 1)).from_buffer_copy(msg or b"\0")
+    sg = (ctypes.c_uint8 * len(sig)).from_buffer_copy(sig) if sig is not None else None
+    _check(load().dil_server_submit(srv, op, level, key, m, len(msg), sg, ctypes.byref(rid)), "dil_server_submit")
+    return rid.value
+
+
+def dil_server_poll(srv, max_n=256, wait_us=1000) -> list:
+    out = (DilResult * max_n)()
+    n = ctypes.c_size_t()
+    _check(load().dil_server_poll(srv, out, max_n, ctypes.byref(n), wait_us), "dil_server_poll")
+    return [out[i] for i in range(n.value)]
+
+
+def dil_server_replay(srv, n, arrival_s, op, level, key, msg, msg_off, sig_in, sig_out, status, ok, latency_s):
+    wall = ctypes.c_double()
+    _check(load().dil_server_replay(srv, n, _ptr(arrival_s), _ptr(op), _ptr(level), _ptr(key), _ptr(msg),
+                                    _ptr(msg_off), _ptr(sig_in), _ptr(sig_out), _ptr(status), _ptr(ok),
+                                    _ptr(latency_s), ctypes.byref(wall)), "dil_server_replay")
+    return wall.value
+
+
+def dil_server_stats(srv) -> tuple[int, int]:
+    b, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().dil_server_stats(srv, ctypes.byref(b), ctypes.byref(r)), "dil_server_stats")
+    return b.value, r.value
 
 
 # ----------------------------------------------------------------- wrapper
