@@ -9,8 +9,16 @@ L2 is flushed (512 MiB write) before every step.  ``value`` is
 (signs + verifies) per second over all ranks; ``e2e`` is the same through the
 host-buffer C entry points with the copies inside the timed region.
 
-Other workloads: ``--workload level3|level5`` (config 3 of the paper-derived
-benchmark set: 10,000 tasks, messages of 32..4096 bytes).
+The same line carries the persistent form of Sign on the same batch (device
+work queue, speculative nonces, CUDA graph) and a served measurement (the
+continuous-batching server over 4096 resident keys per level, mixed 60%
+verify / 40% sign requests of all levels, messages 32 B..16 KB): saturated
+ops/s and p50/p99 latency at half and 90% of saturation.
+
+Other workloads: ``--workload level3|level5`` (10,000 tasks, messages of
+32..4096 bytes), ``--workload mixed`` (persistent Sign of 100,000 Dilithium2 +
+100,000 Dilithium5 tasks in one launch against the plain form) and
+``--workload serving`` (arrival-rate sweep of the served mix to saturation).
 
 ``--impl reference`` times the CPU oracle (test infrastructure) on a bounded
 sample of the same workload on the host cores.
@@ -50,6 +58,8 @@ WORKLOADS = {
     "level2": dict(level=2, n=10000, config=2),
     "level3": dict(level=3, n=10000, config=3),
     "level5": dict(level=5, n=10000, config=3),
+    "mixed": dict(level=5, n=100000, config=4),
+    "serving": dict(level=5, n=60000, config=5),
 }
 
 
@@ -208,6 +218,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     if ranks.rank:
         wl["seeds"] = W.seeds(n, spec["config"], offset=ranks.rank * n)
     ctx = dil.Context(dev)
+    ctx.apply_tuning()
     seeds = torch.from_numpy(wl["seeds"]).cuda()
     msg = torch.from_numpy(wl["msg"]).cuda()
     off = torch.from_numpy(wl["msg_off"]).cuda()
@@ -253,6 +264,27 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     step_ms = float(np.mean(np.add(sign_ms, ver_ms)))
     step_ms_max = ranks.max(step_ms)
     assert bool((status == 0).all()) and bool(ok.all())
+
+    # persistent form of the same Sign batch (graph-captured launch)
+    from paper_2211_12265_gb300 import autotune
+    autotune.apply(ctx, persistent_level=level)
+    job = [dil.sign_job(level, n, sk, msg, off, sig, status)]
+    p_steps = max(1, min(args.steps, 100))
+    for _ in range(max(args.warmup, 3)):
+        dil.dil_sign_persistent(ctx.handle, job, stream)
+    torch.cuda.synchronize()
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(p_steps)]
+    ranks.barrier()
+    for ev in pev:
+        flush.fill_(1)
+        ev[0].record(stream)
+        dil.dil_sign_persistent(ctx.handle, job, stream)
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK
+    assert bool((status == 0).all())
+    p_sign_ms = ranks.max(float(np.mean([e[0].elapsed_time(e[1]) for e in pev])))
+    served = served_summary(dev) if ranks.world == 1 else None
 
     # e2e: host buffers through the host-form C entry points
     h_sk = torch.empty_like(sk, device="cpu").pin_memory()
@@ -309,6 +341,12 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                    "msg_bytes": f"{int(wl['lengths'].min())}-{int(wl['lengths'].max())}",
                    "form": "plain, one launch per phase", "l2": "flushed before every step (512 MiB write)",
                    "parallelism": f"replicas x{ranks.world}"},
+        "forms": {"plain_sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
+                  "persistent_sign_ops_s": ranks.world * n / (p_sign_ms * 1e-3),
+                  "persistent_step_ops_s": ranks.world * n_ops / ((p_sign_ms + ranks.max(float(np.mean(ver_ms))))
+                                                                  * 1e-3),
+                  "persistent_sign_ms": p_sign_ms},
+        "served": served,
         "breakdown": {"sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
                       "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),
                       "sign_ms": sign_mean_ms, "verify_ms": float(np.mean(ver_ms)),
@@ -317,6 +355,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
         "e2e": {"value": ranks.world * n_ops / (e2e_ms * 1e-3), "unit": "ops/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": 2 * args.steps,
+        "gpu_launches_note": "plain timed region: one Sign and one Verify kernel per step",
         "roofline": {"bound": "alu", "kernel": f"k_sign<{level}>", "achieved": achieved,
                      "peak": peak, "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
                      "traffic": traffic, "ops_per_sign": ops / n,
@@ -330,6 +369,113 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     if ranks.rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(level, wl)
     return res
+
+
+def served_summary(dev: int, n: int = 60000) -> dict:
+    """Saturated throughput and p50/p99 latency of the served mix (config 5)."""
+    from paper_2211_12265_gb300 import serving
+    keys = serving.make_keys((2, 3, 5), n_keys=4096, device=dev)
+    with serving.Server(dev, memory_budget=8 << 30, streams=4, max_batch=4096) as srv:
+        for lv in keys:
+            srv.add_keys(lv, *keys[lv])
+        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=100))      # warm-up
+        sat = serving.summarize(req := serving.serving_workload(keys, n, rate=1e9, seed=101), srv.replay(req))
+        rows = []
+        for i, f in enumerate((0.5, 0.9)):
+            rq = serving.serving_workload(keys, n, rate=f * sat["ops_s"], seed=102 + i)
+            r = serving.summarize(rq, srv.replay(rq))
+            r["offered_fraction"] = f
+            rows.append(r)
+    return {"saturated_ops_s": sat["ops_s"], "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB log-uniform, "
+                                                     "4096 resident keys per level, Poisson arrivals",
+            "streams": 4, "at_load": rows}
+
+
+def run_mixed(args, ranks: Ranks) -> dict:
+    """Config 4: persistent Sign of 100,000 Dil2 + 100,000 Dil5 tasks (one
+    graph-captured launch) against the plain one-launch-per-level form."""
+    import torch
+
+    from paper_2211_12265_gb300 import dil
+    n = args.n or 100000
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    ctx = dil.Context(dev)
+    ctx.apply_tuning()
+    data = {}
+    for level in (2, 5):
+        wl = W.workload(4, n)
+        seeds = torch.from_numpy(W.seeds(n, 4 + level, offset=ranks.rank * n)).cuda()
+        msg = torch.from_numpy(wl["msg"]).cuda()
+        off = torch.from_numpy(wl["msg_off"]).cuda()
+        pk, sk = ctx.keygen(level, seeds)
+        sig = torch.empty((n, dil.SIZES[level][2]), dtype=torch.uint8, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        data[level] = (sk, msg, off, sig, st)
+    jobs = [dil.sign_job(2, n, *data[2]), dil.sign_job(5, n, *data[5])]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        ranks.barrier()
+        for ev in evs:
+            flush.fill_(1)
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ranks.max(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])))
+
+    steps = max(1, min(args.steps, 20))
+    t_p = timed(lambda: dil.dil_sign_persistent(ctx.handle, jobs, stream), steps)
+    assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK
+    t_plain = timed(lambda: (dil.dil_sign(ctx.handle, 2, n, *data[2], stream=stream),
+                             dil.dil_sign(ctx.handle, 5, n, *data[5], stream=stream)), steps)
+    ok = all(bool((data[lv][4] == 0).all()) for lv in (2, 5))
+    ctx.close()
+    return {"metric": METRIC, "value": ranks.world * 2 * n / (t_p * 1e-3), "unit": "ops/s", "n_gpus": ranks.world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": t_p, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded PCG64 keys and messages)",
+            "config": {"workload": f"sign-{n}-dilithium2+{n}-dilithium5-persistent", "msg_bytes": 32,
+                       "form": "persistent, one graph-captured launch", "l2": "flushed before every step",
+                       "parallelism": f"replicas x{ranks.world}"},
+            "forms": {"persistent_ops_s": ranks.world * 2 * n / (t_p * 1e-3),
+                      "plain_ops_s": ranks.world * 2 * n / (t_plain * 1e-3), "persistent_ms": t_p,
+                      "plain_ms": t_plain, "all_signed": ok},
+            "gpu_launches": steps}
+
+
+def run_serving(args, ranks: Ranks) -> dict | None:
+    """Config 5: arrival-rate sweep of the served mix, 10% to 120% of saturation."""
+    import torch
+
+    from paper_2211_12265_gb300 import serving
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    keys = serving.make_keys((2, 3, 5), n_keys=4096, device=dev)
+    n = args.n or 60000
+    with serving.Server(dev, memory_budget=8 << 30, streams=4, max_batch=4096) as srv:
+        for lv in keys:
+            srv.add_keys(lv, *keys[lv])
+        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=200))
+        req = serving.serving_workload(keys, n, rate=1e9, seed=201)
+        sat = serving.summarize(req, srv.replay(req))
+        rows = serving.sweep(srv, keys, [f * sat["ops_s"] for f in (0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.2)],
+                             n_per_rate=n, seed=210)
+        batches, carried = srv.stats()
+    best = max(rows + [sat], key=lambda r: r["ops_s"])
+    return {"metric": METRIC, "value": ranks.world * best["ops_s"], "unit": "ops/s", "n_gpus": ranks.world,
+            "steps": len(rows) + 1, "warmup": 1, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Poisson arrivals)",
+            "config": {"workload": "served-mix", "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB "
+                                                        "log-uniform, 4096 resident keys per level",
+                       "requests_per_point": n, "streams": 4, "parallelism": f"replicas x{ranks.world}"},
+            "served": {"saturated": sat, "sweep": rows, "batches": batches, "requests": carried},
+            "gpu_launches": None}
 
 
 def load_traffic(level: int, n: int):
@@ -388,7 +534,14 @@ def main():
     args = parse()
     ranks = Ranks()
     try:
-        res = run_reference(args, ranks) if args.impl == "reference" else run_ours(args, ranks)
+        if args.impl == "reference":
+            res = run_reference(args, ranks)
+        elif args.workload == "mixed":
+            res = run_mixed(args, ranks)
+        elif args.workload == "serving":
+            res = run_serving(args, ranks)
+        else:
+            res = run_ours(args, ranks)
         if res is not None and ranks.rank == 0:
             print(json.dumps(res), flush=True)
     finally:

@@ -69,12 +69,13 @@ int dil_ctx_destroy(dil_ctx *ctx);
  * Tasks that reach the cap get DIL_EITER and an all-zero signature. */
 int dil_set_max_iter(dil_ctx *ctx, int max_iter);
 
-/* Launch shape of the plain kernels for op 0 = keygen, 1 = sign, 2 = verify:
- * warps per CTA (1..8) and warps per task (1, 2 or 4, dividing warps_per_cta;
- * 32 x warps_per_task threads cooperate on one task, the paper's single-warp
- * (1) and four-warp (4) forms).  Defaults: 4 warps per CTA, 1 warp per task.
- * The CTA shares the NTT twiddle tables in shared memory. */
-int dil_set_tuning(dil_ctx *ctx, int op, int warps_per_cta, int warps_per_task);
+/* Launch shape of the plain (and keyed) kernels for op 0 = keygen, 1 = sign,
+ * 2 = verify at `level` (0 = every level): warps per CTA (1..8) and warps per
+ * task (1, 2 or 4, dividing warps_per_cta; 32 x warps_per_task threads
+ * cooperate on one task, the paper's single-warp (1) and four-warp (4) forms).
+ * Defaults: 8 warps per CTA, 2 warps per task.  The CTA shares the NTT
+ * twiddle tables in shared memory. */
+int dil_set_tuning(dil_ctx *ctx, int op, int level, int warps_per_cta, int warps_per_task);
 
 /* Alg 1 (Gen): n 32-byte seeds -> n public keys and n secret keys. */
 int dil_keygen(dil_ctx *ctx, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
@@ -265,6 +266,12 @@ int dil_test_sample_in_ball(dil_ctx *ctx, int level, size_t n, const uint8_t *ct
  * MakeHint(z, r), UseHint(h, r). */
 int dil_test_rounding(dil_ctx *ctx, int level, size_t n, const int32_t *r, const int32_t *z,
                       const uint8_t *h, int32_t *out, void *stream);
+
+/* Failure-detection hook: runs the persistent scheduler's bounded device wait
+ * (poll until a flag reads 0, at most `limit` polls of ~128 ns) on a flag set
+ * to flag_value, synchronously.  *result = DIL_OK when the flag was 0, else
+ * DIL_ETIMEOUT; the context stays usable either way. */
+int dil_test_bounded_wait(dil_ctx *ctx, int flag_value, int limit, int *result);
 
 /* Sustained issue rate of one integer instruction class on the current GPU,
  * in thread-operations per SM clock (clock64 over independent dependency

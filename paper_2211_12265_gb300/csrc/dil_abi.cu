@@ -16,8 +16,9 @@ struct dil_ctx {
     void *ws = nullptr;       // device scratch
     size_t ws_bytes = 0;
     int max_iter = 0;         // 0 = nonce cap
-    int warps[3] = {4, 4, 4}; // warps per CTA for keygen / sign / verify
-    int wpt[3] = {1, 1, 1};   // warps per task
+    // plain-kernel launch shape per operation (keygen / sign / verify) and level (2 / 3 / 5)
+    int warps[3][3] = {{8, 8, 8}, {8, 8, 8}, {8, 8, 8}};   // warps per CTA
+    int wpt[3][3] = {{2, 2, 2}, {2, 2, 2}, {2, 2, 2}};     // warps per task
     // host-form staging (device memory)
     void *stage = nullptr;
     size_t stage_bytes = 0;
@@ -39,6 +40,7 @@ namespace {
 constexpr size_t POLY_BYTES = 256 * sizeof(int32_t);
 
 bool level_ok(int level) { return level == 2 || level == 3 || level == 5; }
+int lidx(int level) { return level == 2 ? 0 : level == 3 ? 1 : 2; }
 
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DIL_ENOMEM : DIL_ECUDA; }
 
@@ -146,13 +148,17 @@ int dil_ctx_destroy(dil_ctx *c) {
     return DIL_OK;
 }
 
-int dil_set_tuning(dil_ctx *c, int op, int warps_per_cta, int warps_per_task) {
+int dil_set_tuning(dil_ctx *c, int op, int level, int warps_per_cta, int warps_per_task) {
     if (!c || op < 0 || op > 2 || warps_per_cta < 1 || warps_per_cta > 8) return DIL_EINVAL;
+    if (level != 0 && !level_ok(level)) return DIL_EINVAL;
     if (warps_per_task != 1 && warps_per_task != 2 && warps_per_task != 4) return DIL_EINVAL;
     if (warps_per_cta % warps_per_task) return DIL_EINVAL;
     std::lock_guard<std::mutex> lk(c->mu);
-    c->warps[op] = warps_per_cta;
-    c->wpt[op] = warps_per_task;
+    for (int li = 0; li < 3; ++li) {
+        if (level && lidx(level) != li) continue;
+        c->warps[op][li] = warps_per_cta;
+        c->wpt[op][li] = warps_per_task;
+    }
     return DIL_OK;
 }
 
@@ -177,7 +183,7 @@ int dil_keygen(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *p
     for (size_t s0 = 0; s0 < n; s0 += chunk) {
         int m = (int)std::min(chunk, n - s0);
         cudaError_t e = dil::launch_keygen(level, m, seeds + 32 * s0, pk + pkb * s0, sk + skb * s0,
-                                           (int32_t *)c->ws, c->warps[0], c->wpt[0], (cudaStream_t)stream);
+                                           (int32_t *)c->ws, c->warps[0][lidx(level)], c->wpt[0][lidx(level)], (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -204,7 +210,7 @@ int dil_sign_ex(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_
         cudaError_t e = dil::launch_sign(level, m, sk + skb * s0, msg, msg_off + s0, sig + sigb * s0,
                                          task_status ? task_status + s0 : nullptr,
                                          iterations ? iterations + s0 : nullptr, (int32_t *)c->ws, max_iter,
-                                         c->warps[1], c->wpt[1], (cudaStream_t)stream);
+                                         c->warps[1][lidx(level)], c->wpt[1][lidx(level)], (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -231,7 +237,8 @@ int dil_verify(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t
     for (size_t s0 = 0; s0 < n; s0 += chunk) {
         int m = (int)std::min(chunk, n - s0);
         cudaError_t e = dil::launch_verify(level, m, pk + pkb * s0, msg, msg_off + s0, sig + sigb * s0, ok + s0,
-                                           (int32_t *)c->ws, c->warps[2], c->wpt[2], (cudaStream_t)stream);
+                                           (int32_t *)c->ws, c->warps[2][lidx(level)], c->wpt[2][lidx(level)],
+                                           (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -420,7 +427,8 @@ int dil_sign_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *
         cudaError_t e = dil::launch_sign_keyed(ks->level, m, (int)ks->n, key_idx + s0, ks->sk, ks->keys, msg,
                                                msg_off + s0, sig + sigb * s0,
                                                task_status ? task_status + s0 : nullptr, nullptr, (int32_t *)c->ws,
-                                               max_iter, c->warps[1], c->wpt[1], (cudaStream_t)stream);
+                                               max_iter, c->warps[1][lidx(ks->level)], c->wpt[1][lidx(ks->level)],
+                                               (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -444,7 +452,8 @@ int dil_verify_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t
         int m = (int)std::min(chunk, n - s0);
         cudaError_t e = dil::launch_verify_keyed(ks->level, m, (int)ks->n, key_idx + s0, ks->pk, ks->keys, ks->tr,
                                                  msg, msg_off + s0, sig + sigb * s0, ok + s0, (int32_t *)c->ws,
-                                                 c->warps[2], c->wpt[2], (cudaStream_t)stream);
+                                                 c->warps[2][lidx(ks->level)], c->wpt[2][lidx(ks->level)],
+                                                 (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return DIL_OK;
@@ -624,6 +633,12 @@ int dil_test_rounding(dil_ctx *c, int level, size_t n, const int32_t *r, const i
     TEST_PROLOGUE(c)
     if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!r || !z || !h || !out))) return DIL_EINVAL;
     return status_of(dil::launch_test_rounding(level, (int)n, r, z, h, out, (cudaStream_t)stream));
+}
+
+int dil_test_bounded_wait(dil_ctx *c, int flag_value, int limit, int *result) {
+    TEST_PROLOGUE(c)
+    if (!result || limit < 1 || limit > (1 << 24)) return DIL_EINVAL;
+    return status_of(dil::test_bounded_wait(flag_value, limit, result));
 }
 
 int dil_test_issue_rate(dil_ctx *c, int op, double *thread_ops_per_sm_clk) {

@@ -109,6 +109,8 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
                                 int device, cudaStream_t s);
 // Reads the device error word of the last launch on ws (synchronous).
 int persist_error(void *ws);
+// Runs the scheduler's bounded wait on a flag holding flag_value (synchronous).
+cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host);
 
 // test-only issue-rate probe (thread-ops per SM clock)
 cudaError_t measure_issue_rate(int op, double *rate);

@@ -31,6 +31,21 @@ constexpr int PERSIST_META_POLYS = 1;   // mu (64 B) and rho' (64 B) of a slot's
 
 __device__ __forceinline__ int ld_l2(const int *p) { return __ldcg(p); }
 
+// Waits until *p reads 0, at most `limit` polls; false when the limit ran out.
+__device__ __forceinline__ bool wait_until_zero(int *p, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        if (atomicAdd(p, 0) == 0) return true;
+        __nanosleep(128);
+    }
+    return false;
+}
+
+// Test hook for the bounded wait: one thread waits on `flag` and records the
+// outcome (DIL_OK or DIL_ETIMEOUT) in *result.
+__global__ void k_test_bounded_wait(int *flag, int limit, int *result) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *result = wait_until_zero(flag, limit) ? DIL_OK : DIL_ETIMEOUT;
+}
+
 __device__ __forceinline__ const PersistJob &job_of(const PersistJobs &J, int t, int &local) {
     int j = 0;
     while (j + 1 < J.njobs && t >= J.job[j + 1].start) ++j;
@@ -152,14 +167,7 @@ __device__ void own_task(const PersistCtx &pc, int t, const PersistJob &jb, int 
     if (leader) {
         atomicExch(&pc.slot_task[slot], -1);
         __threadfence();
-        int waited = 0;
-        while (atomicAdd(&tk.helpers, 0) != 0) {
-            if (++waited > PERSIST_SPIN_LIMIT) {
-                atomicExch(&pc.q->error, DIL_ETIMEOUT);
-                break;
-            }
-            __nanosleep(128);
-        }
+        if (!wait_until_zero(&tk.helpers, PERSIST_SPIN_LIMIT)) atomicExch(&pc.q->error, DIL_ETIMEOUT);
         gs.claim2 = (atomicOr(&tk.best_r, 0) == INT_MAX) ? 1 : 0;
     }
     group_sync<P>(bar);
@@ -374,6 +382,22 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
             break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host) {
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+    if (e != cudaSuccess) return e;
+    int h[2] = {flag_value, -99};
+    e = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_test_bounded_wait<<<1, 32>>>(d, limit, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e == cudaSuccess) *result_host = h[1];
+    return e;
 }
 
 int persist_error(void *ws) {

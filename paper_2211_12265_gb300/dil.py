@@ -51,7 +51,7 @@ def load() -> ctypes.CDLL:
                 "dil_ctx_create": [I, S, P],
                 "dil_ctx_destroy": [P],
                 "dil_set_max_iter": [P, I],
-                "dil_set_tuning": [P, I, I, I],
+                "dil_set_tuning": [P, I, I, I, I],
                 "dil_keygen": [P, I, S, P, P, P, P],
                 "dil_sign": [P, I, S, P, P, P, P, P, P],
                 "dil_sign_ex": [P, I, S, P, P, P, P, P, P, P],
@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_sample_in_ball": [P, I, S, P, P, P],
                 "dil_test_rounding": [P, I, S, P, P, P, P, P],
                 "dil_test_issue_rate": [P, I, P],
+                "dil_test_bounded_wait": [P, I, I, P],
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
                 "dil_persistent_status": [P, P],
@@ -148,8 +149,8 @@ def dil_set_max_iter(ctx: int, max_iter: int) -> None:
     _check(load().dil_set_max_iter(ctx, max_iter), "dil_set_max_iter")
 
 
-def dil_set_tuning(ctx: int, op: int, warps_per_cta: int, warps_per_task: int = 1) -> None:
-    _check(load().dil_set_tuning(ctx, op, warps_per_cta, warps_per_task), "dil_set_tuning")
+def dil_set_tuning(ctx: int, op: int, warps_per_cta: int, warps_per_task: int = 1, level: int = 0) -> None:
+    _check(load().dil_set_tuning(ctx, op, level, warps_per_cta, warps_per_task), "dil_set_tuning")
 
 
 def dil_keygen(ctx, level, n, seeds, pk, sk, stream=None):
@@ -233,6 +234,12 @@ def dil_test_issue_rate(ctx, op: int) -> float:
     """Thread-ops per SM clock of one integer instruction class (see dil.h)."""
     r = ctypes.c_double()
     _check(load().dil_test_issue_rate(ctx, op, ctypes.byref(r)), "dil_test_issue_rate")
+    return r.value
+
+
+def dil_test_bounded_wait(ctx, flag_value: int, limit: int) -> int:
+    r = ctypes.c_int()
+    _check(load().dil_test_bounded_wait(ctx, flag_value, limit, ctypes.byref(r)), "dil_test_bounded_wait")
     return r.value
 
 
@@ -366,8 +373,14 @@ class Context:
         except Exception:
             pass
 
-    def set_tuning(self, op: int, warps_per_cta: int, warps_per_task: int = 1) -> None:
-        dil_set_tuning(self.handle, op, warps_per_cta, warps_per_task)
+    def set_tuning(self, op: int, warps_per_cta: int, warps_per_task: int = 1, level: int = 0) -> None:
+        dil_set_tuning(self.handle, op, warps_per_cta, warps_per_task, level)
+
+    def apply_tuning(self, table: dict | None = None) -> None:
+        """Applies an autotuner table (see autotune.py; the committed GB300
+        table by default)."""
+        from . import autotune
+        autotune.apply(self, table)
 
     def set_max_iter(self, max_iter: int) -> None:
         dil_set_max_iter(self.handle, max_iter)

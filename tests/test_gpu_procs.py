@@ -176,7 +176,7 @@ def test_launch_shapes_bit_exact(orc, level, shape):
     c = dil.Context(0)
     try:
         for op in range(3):
-            c.set_tuning(op, *shape)
+            c.set_tuning(op, shape[0], shape[1])
         pk, sk = gpu_keygen(c, level, seeds)
         sig, st, it = gpu_sign(c, level, osk, msg, off)
         bad = osig.copy()
