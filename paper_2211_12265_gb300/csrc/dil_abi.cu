@@ -443,7 +443,7 @@ int dil_verify_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t
     DeviceGuard g(c->device);
     size_t pkb, skb, sigb;
     sizes_of(ks->level, pkb, skb, sigb);
-    const size_t per = dil::scratch_polys(dil::OP_VERIFY, ks->level) * POLY_BYTES;
+    const size_t per = dil::keyed_verify_polys(ks->level) * POLY_BYTES;
     size_t chunk = std::min<size_t>(n, c->budget / per);
     if (chunk == 0) return DIL_ENOMEM;
     int rc = ensure_ws(c, chunk * per);

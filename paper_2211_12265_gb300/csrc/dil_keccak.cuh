@@ -24,9 +24,13 @@ static __constant__ uint64_t c_keccak_rc[24] = {
     0x8000000000008002ull, 0x8000000000000080ull, 0x000000000000800Aull, 0x800000008000000Aull,
     0x8000000080008081ull, 0x8000000000008080ull, 0x0000000080000001ull, 0x8000000080008008ull};
 
-// FIPS 202 rho rotation offsets, indexed by x + 5y.
-static __constant__ uint8_t c_keccak_rho[25] = {0,  1,  62, 28, 27, 36, 44, 6,  55, 20, 3,  10, 43,
-                                                25, 39, 41, 45, 15, 21, 8,  18, 2,  61, 56, 14};
+// FIPS 202 rho rotation offset of lane (x, y).  Each row's five offsets are
+// packed as 6-bit fields of one immediate, so lanes asking for different
+// offsets do not serialise on a constant-memory table.
+__device__ __forceinline__ int rho_offset(int x, int y) {
+    const uint32_t row = y == 0 ? 0x1B73E040u : y == 1 ? 0x14DC6B24u : y == 2 ? 0x2766B283u : y == 3 ? 0x0854FB69u : 0x0EE3D092u;
+    return (int)((row >> (6 * x)) & 63u);
+}
 
 // Per-thread shuffle sources and rotation for one warp-level Keccak instance.
 struct KLane {
@@ -52,7 +56,7 @@ __device__ __forceinline__ KLane klane_init(int lane) {
     k.b0 = (x + 3 * y) % 5 + 5 * x;
     k.b1 = (x1 + 3 * y) % 5 + 5 * x1;
     k.b2 = (x2 + 3 * y) % 5 + 5 * x2;
-    int r = c_keccak_rho[t];
+    int r = rho_offset(x, y);
     k.rot = r & 31;
     k.swap = r >= 32;
     k.lane0 = lane == 0;

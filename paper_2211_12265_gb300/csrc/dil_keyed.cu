@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256, 4) k_verify_keyed(int n, int n_keys, cons
     }
     const uint64_t m0 = off[task], m1 = off[task + 1];
     int r = verify_task<LEVEL, P, true>(pk + (size_t)key * V::PK, msg + m0, (size_t)(m1 - m0),
-                                        sig + (size_t)task * V::SIG, scratch + (size_t)task * S::VERIFY_POLYS * N,
+                                        sig + (size_t)task * V::SIG, scratch + (size_t)task * S::KEYED_VERIFY_POLYS * N,
                                         *v.gs, *v.ws, v.zt, v.izt, v.g, v.bar, v.lane,
                                         keys + (size_t)key * S::KEY_POLYS * N, tr + (size_t)key * 32);
     if (v.g == 0 && v.lane == 0) ok[task] = (uint8_t)r;
@@ -112,9 +112,18 @@ template <int LEVEL>
 static size_t key_polys_of() { return Scratch<LEVEL>::KEY_POLYS; }
 template <int LEVEL>
 static size_t itr_polys_of() { return Scratch<LEVEL>::ITR_POLYS; }
+template <int LEVEL>
+static size_t keyed_verify_polys_of() { return Scratch<LEVEL>::KEYED_VERIFY_POLYS; }
 
 size_t key_polys(int level) {
     return level == 2 ? key_polys_of<2>() : level == 3 ? key_polys_of<3>() : level == 5 ? key_polys_of<5>() : 0;
+}
+
+size_t keyed_verify_polys(int level) {
+    return level == 2   ? keyed_verify_polys_of<2>()
+           : level == 3 ? keyed_verify_polys_of<3>()
+           : level == 5 ? keyed_verify_polys_of<5>()
+                        : 0;
 }
 
 size_t keyed_sign_polys(int level) {

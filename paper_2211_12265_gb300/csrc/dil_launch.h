@@ -38,6 +38,7 @@ cudaError_t launch_verify(int level, int n, const uint8_t *pk, const uint8_t *ms
 // per-task scratch of a keyed Sign (y, y^, w, z)
 size_t key_polys(int level);
 size_t keyed_sign_polys(int level);
+size_t keyed_verify_polys(int level);
 cudaError_t launch_key_prepare(int level, int n, const uint8_t *pk, const uint8_t *sk, int32_t *keys, uint8_t *tr,
                                int warps, int p, cudaStream_t s);
 // key indices outside [0, n_keys) are rejected per task (status DIL_EINVAL / ok 0)

@@ -56,20 +56,18 @@ __global__ void k_test_ntt(int n, const int32_t *in, int32_t *out, int inverse) 
     }
 }
 
+// Covers the single, pair and six-sponge forms: polynomial 0 alone, 1-2 as a
+// pair, the rest as one range (six at a time, then the tail).
 template <int LEVEL>
 __global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
     stage_bytes(gs.rho, rho + (size_t)item * 32, 32, lane);
     __syncwarp();
-    for (int i = 0; i < V::K; ++i)
-        for (int j = 0; j < V::L; ++j) {
-            expand_a_poly(gs.rho, i, j, ws.buf, ws.sq, lane);
-            int32_t a[8];
-            read_buf_l2(a, ws.buf, lane);
-            __syncwarp();
-            store_l2(out + ((size_t)item * V::K * V::L + i * V::L + j) * N, a, lane);
-        }
+    int32_t *o = out + (size_t)item * V::K * V::L * N;
+    expand_a_range<LEVEL>(gs.rho, 0, 1, o, ws, lane);
+    expand_a_range<LEVEL>(gs.rho, 1, 3, o, ws, lane);
+    expand_a_range<LEVEL>(gs.rho, 3, V::K * V::L, o, ws, lane);
 }
 
 template <int LEVEL>
@@ -87,16 +85,36 @@ __global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
     }
 }
 
+// Even items: all l polynomials through six-sponge batches (with a pair or
+// single tail where l is not a multiple of six); odd items: single, pair and
+// the rest.
 template <int LEVEL>
 __global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out) {
     PRIM_PROLOGUE
     using V = Lv<LEVEL>;
     stage_bytes(gs.rhop, rhop + (size_t)item * 64, 64, lane);
     __syncwarp();
-    for (int j = 0; j < V::L; ++j) {
-        int32_t a[8];
+    int32_t *o = out + (size_t)item * V::L * N;
+    int32_t a[8], b[8];
+    int j = 0;
+    if (item & 1) {
+        expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item], a, ws.sq, lane);
+        store_l0(o, a, lane);
+        expand_mask_pair<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + 1, kappa[item] + 2, a, b, ws.sq, ws.sq2,
+                                              lane);
+        store_l0(o + N, a, lane);
+        store_l0(o + 2 * N, b, lane);
+        j = 3;
+    }
+    while (V::L - j >= 3 || (j == 0 && V::L > 0)) {
+        const int c = min(K6_STATES, V::L - j);
+        expand_mask_six<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + j, c, o + j * N, ws.kst, ws.kpi(), ws.win,
+                                             lane);
+        j += c;
+    }
+    for (; j < V::L; ++j) {
         expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + j, a, ws.sq, lane);
-        store_l0(out + ((size_t)item * V::L + j) * N, a, lane);
+        store_l0(o + j * N, a, lane);
     }
 }
 

@@ -18,12 +18,24 @@
 
 namespace dil {
 
-// Per-warp shared memory.
+// Per-warp shared memory.  The six-state sponges (states, field windows) and
+// the one- and two-state ones (sampled polynomials, squeezed blocks) are never
+// live at the same time and share one area; buf doubles as the six-state
+// permutation's pi exchange.
 struct __align__(16) WarpSmem {
-    int32_t buf[288];    // NTT exchanges / sampled polynomial (padded)
-    int32_t buf2[288];   // second sampled polynomial of a pair
-    uint8_t sq[688];     // squeezed SHAKE blocks (5 x 136 + slack)
-    uint8_t sq2[688];    // squeezed blocks of the second sponge of a pair
+    int32_t buf[K6_PI_WORDS];      // NTT exchanges / sampled polynomial (padded) / keccak6 pi exchange
+    union {
+        struct {
+            int32_t buf2[288];     // second sampled polynomial of a pair
+            uint8_t sq[688];       // squeezed SHAKE blocks (5 x 136 + slack)
+            uint8_t sq2[688];      // squeezed blocks of the second sponge of a pair
+        };
+        struct {
+            uint32_t kst[K6_STATES * K6_WORDS];   // six Keccak states
+            uint32_t win[K6_STATES * 38];         // ExpandMask field windows
+        };
+    };
+    __device__ uint32_t *kpi() { return reinterpret_cast<uint32_t *>(buf); }
 };
 
 // Per-task (per-group) shared memory.  Every region is 8-byte aligned.
@@ -60,7 +72,7 @@ struct Units {
     static constexpr int SIZE = (M >= 2 * P) ? 2 : 1;
 };
 
-__device__ __forceinline__ void load_l2(int32_t v[8], const int32_t *__restrict__ p, int lane) {
+__device__ __forceinline__ void load_l2(int32_t v[8], const int32_t *p, int lane) {
     const int4 *q = reinterpret_cast<const int4 *>(p + 8 * lane);
     int4 a = q[0], b = q[1];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -81,7 +93,7 @@ __device__ __forceinline__ void store_l2(int32_t *p, const int32_t v[8], int lan
     q[1] = make_int4(v[4], v[5], v[6], v[7]);
 }
 
-__device__ __forceinline__ void load_l0(int32_t v[8], const int32_t *__restrict__ p, int lane) {
+__device__ __forceinline__ void load_l0(int32_t v[8], const int32_t *p, int lane) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = p[lane + 32 * m];
 }
@@ -140,38 +152,92 @@ template <int LEVEL> struct Scratch {
     static constexpr int Z = W + V::K;
     static constexpr int ITR_POLYS = Z + V::L;
     static constexpr int SIGN_POLYS = PRE_POLYS + ITR_POLYS;
-    static constexpr int GEN_POLYS = V::L;     // s^1
-    static constexpr int VERIFY_POLYS = V::L;  // z^
+    static constexpr int GEN_POLYS = V::L + V::K * V::L;      // s^1, A^
+    static constexpr int VERIFY_POLYS = V::L + V::K * V::L;   // z^, A^
+    static constexpr int KEYED_VERIFY_POLYS = V::L;           // z^ (A^ is resident)
     // resident key: the Sign precomputation followed by NTT(t1 2^d)
     static constexpr int T1H = PRE_POLYS;
     static constexpr int KEY_POLYS = T1H + V::K;
 };
 
-// acc = sum_j A^_ij o v^_j (pointwise Montgomery products) for one row i of A^,
-// sampling A^ on the fly two polynomials at a time; v^_j (layout L2) are the
-// l polynomials at `vhat`.  acc is overwritten.
-__device__ __forceinline__ void accumulate_a_row(int32_t acc[8], const uint8_t *rho, int i, int l,
-                                                 const int32_t *vhat, WarpSmem &ws, int lane) {
+// Warp g's share [share_lo(g), share_lo(g + 1)) of M polynomials cut into P
+// contiguous ranges (so that each warp can batch its sponges).
+template <int M, int P>
+__device__ __forceinline__ int share_lo(int g) { return g * M / P; }
+
+// A^_p (p = i l + j) for p in [lo, hi) into out + p N in index order: six
+// sponges at a time while at least three remain, then a pair or a single.
+template <int LEVEL>
+__device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out, WarpSmem &ws, int lane) {
+    constexpr int L = Lv<LEVEL>::L;
+    int p = lo;
+    while (hi - p >= 3) {
+        const int c = min(K6_STATES, hi - p);
+        expand_a_six<L>(rho, p, c, out + p * N, ws.kst, ws.kpi(), lane);
+        p += c;
+    }
+    int32_t a[8];
+    if (hi - p == 2) {
+        expand_a_pair(rho, p / L, p % L, (p + 1) / L, (p + 1) % L, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
+        read_buf_l2(a, ws.buf2, lane);
+        store_l2(out + (p + 1) * N, a, lane);
+    } else if (hi - p == 1) {
+        expand_a_poly(rho, p / L, p % L, ws.buf, ws.sq, lane);
+    }
+    if (hi - p >= 1) {
+        read_buf_l2(a, ws.buf, lane);
+        store_l2(out + p * N, a, lane);
+    }
+    __syncwarp();
+}
+
+// y_j = ExpandMask(rho', kappa + j) in coefficient order to y + j N and
+// y^_j = NTT(y_j) in index order to yh + j N, for j in [lo, hi).
+template <int LEVEL>
+__device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi, int32_t *y, int32_t *yh,
+                                  WarpSmem &ws, const int32_t *zt, int lane) {
+    using V = Lv<LEVEL>;
+    int32_t r[8], a[8];
+    int j = lo;
+    while (hi - j >= 3) {
+        const int c = min(K6_STATES, hi - j);
+        expand_mask_six<V::ZBITS, V::GAMMA1>(rhop, kappa + j, c, y + j * N, ws.kst, ws.kpi(), ws.win, lane);
+        __syncwarp();
+        for (int u = j; u < j + c; ++u) {
+            load_l0(r, y + u * N, lane);
+            ntt_fwd(r, ws.buf, zt, lane);
+            store_l2(yh + u * N, r, lane);
+        }
+        j += c;
+    }
+    if (hi - j == 2) {
+        expand_mask_pair<V::ZBITS, V::GAMMA1>(rhop, kappa + j, kappa + j + 1, r, a, ws.sq, ws.sq2, lane);
+        store_l0(y + (j + 1) * N, a, lane);
+        ntt_fwd(a, ws.buf, zt, lane);
+        store_l2(yh + (j + 1) * N, a, lane);
+    } else if (hi - j == 1) {
+        expand_mask_poly<V::ZBITS, V::GAMMA1>(rhop, kappa + j, r, ws.sq, lane);
+    }
+    if (hi - j >= 1) {
+        store_l0(y + j * N, r, lane);
+        ntt_fwd(r, ws.buf, zt, lane);
+        store_l2(yh + j * N, r, lane);
+    }
+}
+
+// acc = sum_j A^_ij o v^_j (pointwise Montgomery products) for one row i of A^
+// (ahat: the row's l polynomials, index order; read through L2 since another
+// warp or kernel may have written them); v^_j (index order) at `vhat`.
+__device__ __forceinline__ void accumulate_row(int32_t acc[8], const int32_t *ahat, int l, const int32_t *vhat,
+                                               int lane) {
     int32_t a[8], v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = 0;
-    for (int j = 0; j < l; j += 2) {
-        const bool two = j + 1 < l;
-        if (two)
-            expand_a_pair(rho, i, j, i, j + 1, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
-        else
-            expand_a_poly(rho, i, j, ws.buf, ws.sq, lane);
-        read_buf_l2(a, ws.buf, lane);
+    for (int j = 0; j < l; ++j) {
+        load_l2_cg(a, ahat + j * N, lane);
         load_l2(v, vhat + j * N, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], v[m]);
-        if (two) {
-            read_buf_l2(a, ws.buf2, lane);
-            load_l2(v, vhat + (j + 1) * N, lane);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], v[m]);
-        }
-        __syncwarp();
     }
 }
 
@@ -231,10 +297,13 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
             store_l2(scratch + jj * N, r, lane);
         }
     }
+    // A^ = ExpandA(rho) into scratch after s^1  (l.3)
+    constexpr int KL = V::K * V::L;
+    expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
     group_sync<P>(bar);
     // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)  (l.3, l.5, l.6)
     for (int i = g; i < V::K; i += P) {
-        accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
+        accumulate_row(acc, scratch + (V::L + i * V::L) * N, V::L, scratch, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = reduce_q(acc[m]);
         ntt_inv(acc, ws.buf, izt, lane);
@@ -301,23 +370,9 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
         squeeze_words(lo, hi, gs.rhop, 8, lane);
         __syncwarp();
     }
-    // A^ = ExpandA(rho)  (l.3); k l is even, so units are pairs when P allows
+    // A^ = ExpandA(rho)  (l.3)
     constexpr int KL = V::K * V::L;
-    constexpr int UA = Units<KL, P>::SIZE;
-    for (int p = UA * g; p < KL; p += UA * P) {
-        int32_t a[8];
-        if (UA == 2) {
-            expand_a_pair(gs.rho, p / V::L, p % V::L, (p + 1) / V::L, (p + 1) % V::L, ws.buf, ws.buf2, ws.sq,
-                          ws.sq2, lane);
-            read_buf_l2(a, ws.buf2, lane);
-            store_l2(scratch + (S::AH + p + 1) * N, a, lane);
-        } else {
-            expand_a_poly(gs.rho, p / V::L, p % V::L, ws.buf, ws.sq, lane);
-        }
-        read_buf_l2(a, ws.buf, lane);
-        store_l2(scratch + (S::AH + p) * N, a, lane);
-        __syncwarp();
-    }
+    expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, ws, lane);
     // s^1, s^2, t^0  (l.4): polynomials u = 0 .. l + 2k - 1 across the group
     for (int u = g; u < V::L + 2 * V::K; u += P) {
         if (u < V::L) {
@@ -366,21 +421,7 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
     if (g == 0) gs.rho[lane] = __ldg(pk + lane);
     group_sync<P>(bar);
     constexpr int KL = V::K * V::L;
-    constexpr int UA = Units<KL, P>::SIZE;
-    for (int p = UA * g; p < KL; p += UA * P) {
-        int32_t a[8];
-        if (UA == 2) {
-            expand_a_pair(gs.rho, p / V::L, p % V::L, (p + 1) / V::L, (p + 1) % V::L, ws.buf, ws.buf2, ws.sq,
-                          ws.sq2, lane);
-            read_buf_l2(a, ws.buf2, lane);
-            store_l2(key + (S::AH + p + 1) * N, a, lane);
-        } else {
-            expand_a_poly(gs.rho, p / V::L, p % V::L, ws.buf, ws.sq, lane);
-        }
-        read_buf_l2(a, ws.buf, lane);
-        store_l2(key + (S::AH + p) * N, a, lane);
-        __syncwarp();
-    }
+    expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), key + S::AH * N, ws, lane);
     // s^1, s^2, t^0 (when the secret key is resident) and NTT(t1 2^d)
     const int first = sk ? 0 : V::L + 2 * V::K;
     for (int u = first + g; u < V::L + 3 * V::K; u += P) {
@@ -422,20 +463,8 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
     volatile int *vflag = &gs.flag;
     int32_t r[8], a[8], acc[8], ch[8];
     // y = ExpandMask(rho', kappa); y^ = NTT(y)  (l.6)
-    constexpr int UY = Units<V::L, P>::SIZE;
-    for (int j = UY * g; j < V::L; j += UY * P) {
-        if (UY == 2 && j + 1 < V::L) {
-            expand_mask_pair<V::ZBITS, V::GAMMA1>(gs.rhop, kappa + j, kappa + j + 1, r, a, ws.sq, ws.sq2, lane);
-            store_l0(itr + (S::Y + j + 1) * N, a, lane);
-            ntt_fwd(a, ws.buf, zt, lane);
-            store_l2(itr + (S::YH + j + 1) * N, a, lane);
-        } else {
-            expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa + j, r, ws.sq, lane);
-        }
-        store_l0(itr + (S::Y + j) * N, r, lane);
-        ntt_fwd(r, ws.buf, zt, lane);
-        store_l2(itr + (S::YH + j) * N, r, lane);
-    }
+    expand_mask_range<LEVEL>(gs.rhop, kappa, share_lo<V::L, P>(g), share_lo<V::L, P>(g + 1), itr + S::Y * N,
+                             itr + S::YH * N, ws, zt, lane);
     group_sync<P>(bar);
     // w = INTT(A^ o y^); w1 = HighBits(w)  (l.7-8)
     for (int i = g; i < V::K; i += P) {
@@ -642,6 +671,10 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         ntt_fwd(r, ws.buf, zt, lane);
         store_l2(scratch + j * N, r, lane);
     }
+    // A^ = ExpandA(rho) into scratch after z^ (unless resident)
+    constexpr int KL = V::K * V::L;
+    if (!KEYED)
+        expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
     // mu = H(H(rho || t1) || M)  (l.2), on the last warp
     if (g == P - 1) {
         uint32_t lo = 0, hi = 0;
@@ -662,21 +695,13 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     // c^ = NTT(SampleInBall(c~))  (l.3)
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)  (l.4-5)
+    using S = Scratch<LEVEL>;
+    const int32_t *ahat = KEYED ? key + S::AH * N : scratch + V::L * N;
     for (int i = g; i < V::K; i += P) {
+        accumulate_row(acc, ahat + i * V::L * N, V::L, scratch, lane);
         if (KEYED) {
-            using S = Scratch<LEVEL>;
-            int32_t a[8], zv[8];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] = 0;
-            for (int j = 0; j < V::L; ++j) {
-                load_l2_cg(a, key + (S::AH + i * V::L + j) * N, lane);
-                load_l2(zv, scratch + j * N, lane);
-#pragma unroll
-                for (int m = 0; m < 8; ++m) acc[m] += mont_mul(a[m], zv[m]);
-            }
             load_l2_cg(r, key + (S::T1H + i) * N, lane);
         } else {
-            accumulate_a_row(acc, gs.rho, i, V::L, scratch, ws, lane);
             unpack_poly_l0<10>(r, pk + 32 + i * V::POLYT1, 0, ws, lane);
 #pragma unroll
             for (int m = 0; m < 8; ++m) r[m] = (-r[m]) << D;   // t1 2^d, t1 stored as 0 - field

@@ -5,6 +5,7 @@
 // permutation (keccak_f2), for instruction-level parallelism.
 #pragma once
 #include "dil_keccak.cuh"
+#include "dil_keccak6.cuh"
 #include "dil_ntt.cuh"
 
 namespace dil {
@@ -78,6 +79,85 @@ __device__ __forceinline__ void expand_a_pair(const uint8_t *rho, int i0, int j0
         __syncwarp();
         if (c0 >= N && c1 >= N) break;
         keccak_f2(lo0, hi0, lo1, hi1);
+    }
+}
+
+// Six-instance ExpandA: polynomials p0 .. p0 + count - 1 (count <= 6) of A^
+// (p = i l + j), rejection-sampled with the same warp vote straight from the
+// states' squeezed blocks into global memory, coefficient c of polynomial p at
+// out[(p - p0) 256 + c] (index order).  rho: 32 bytes of shared memory.
+template <int L>
+__device__ __forceinline__ void expand_a_six(const uint8_t *rho, int p0, int count, int32_t *out, uint32_t *kst,
+                                             uint32_t *kpi, int lane) {
+    keccak6_seed(
+        kst, reinterpret_cast<const uint32_t *>(rho), 8,
+        [&](int g) { const int p = p0 + g; return (uint32_t)(p % L) | ((uint32_t)(p / L) << 8) | (0x1Fu << 16); },
+        count, 168, lane);
+    keccak6_permute(kst, kpi);
+    int ctr[K6_STATES];
+#pragma unroll
+    for (int g = 0; g < K6_STATES; ++g) ctr[g] = 0;
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+        bool more = false;
+#pragma unroll
+        for (int g = 0; g < K6_STATES; ++g) {
+            if (g < count && ctr[g] < N) {
+                const uint8_t *sq = reinterpret_cast<const uint8_t *>(kst + K6_WORDS * g);
+                int32_t *dst = out + g * N;
+                int c = ctr[g];
+#pragma unroll
+                for (int rnd = 0; rnd < 2; ++rnd) {
+                    const int k = rnd * 32 + lane;
+                    const bool valid = k < 56;
+                    const uint32_t v = valid ? (get_field(sq, 24 * k, 24) & 0x7FFFFFu) : 0u;
+                    const bool acc = valid && v < (uint32_t)Q;
+                    const uint32_t mask = __ballot_sync(FULL, acc);
+                    const int pos = c + __popc(mask & lanemask_lt(lane));
+                    if (acc && pos < N) dst[pos] = (int32_t)v;
+                    c += __popc(mask);
+                }
+                ctr[g] = c;
+                more |= c < N;
+            }
+        }
+        if (!more) break;
+        keccak6_permute(kst, kpi);
+    }
+}
+
+// Six-instance ExpandMask: y_j for nonces nonce0 .. nonce0 + count - 1
+// (count <= 6), coefficient c of y_j at out[j 256 + c] (natural order).
+// After each permutation the 136-byte block is copied behind the last 8 bytes
+// of the previous one into a per-instance window (win: 6 x 38 words), and the
+// fields whose last bit lies in this block are extracted.
+template <int ZBITS, int32_t GAMMA1>
+__device__ __forceinline__ void expand_mask_six(const uint8_t *rhop, int nonce0, int count, int32_t *out,
+                                                uint32_t *kst, uint32_t *kpi, uint32_t *win, int lane) {
+    keccak6_seed(
+        kst, reinterpret_cast<const uint32_t *>(rhop), 16,
+        [&](int g) { return ((uint32_t)(nonce0 + g) & 0xFFFFu) | (0x1Fu << 16); }, count, 136, lane);
+    constexpr int BLOCKS = (N * ZBITS / 8 + 135) / 136;
+#pragma unroll 1
+    for (int b = 0; b < BLOCKS; ++b) {
+        keccak6_permute(kst, kpi);
+        if (lane < 2 * K6_STATES) {   // carry: the previous block's last 8 bytes
+            const int g = lane >> 1, k = lane & 1;
+            win[38 * g + k] = win[38 * g + 34 + k];
+        }
+        __syncwarp();
+        for (int w = lane; w < K6_STATES * 34; w += 32) {
+            const int g = w / 34, k = w % 34;
+            win[38 * g + 2 + k] = kst[K6_WORDS * g + k];
+        }
+        __syncwarp();
+        const int c_lo = (1088 * b) / ZBITS;
+        const int c_hi = min(N, (1088 * (b + 1)) / ZBITS);
+        for (int g = 0; g < count; ++g) {
+            const uint8_t *wb = reinterpret_cast<const uint8_t *>(win + 38 * g);
+            for (int c = c_lo + lane; c < c_hi; c += 32)
+                out[g * N + c] = GAMMA1 - (int32_t)get_field(wb, ZBITS * c - (1088 * b - 64), ZBITS);
+        }
+        __syncwarp();
     }
 }
 
