@@ -100,7 +100,7 @@ __device__ __forceinline__ void keccak_round(uint32_t &lo, uint32_t &hi, const K
 static __device__ __noinline__ uint2 keccak_f_impl(uint2 s) {
     const KLane k = klane_init(threadIdx.x & 31);
     uint32_t lo = s.x, hi = s.y;
-#pragma unroll 4
+#pragma unroll 2
     for (int r = 0; r < 24; ++r) keccak_round(lo, hi, k, c_keccak_rc[r]);
     return make_uint2(lo, hi);
 }

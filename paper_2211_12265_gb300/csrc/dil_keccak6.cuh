@@ -13,9 +13,10 @@
 // stores its five rotated lanes at their destinations (a rotation by >= 32 is
 // folded into the store by swapping the two words) and reads back its new
 // row.  The buffer keeps low and high words in separate planes, slot j of the
-// lane for row Y of instance g at word 30 j + 5 g + Y of its plane, so the row
-// reads are at fixed offsets and both they and the scattered stores hit 30
-// distinct banks.  Per instance-round that is 2.7 shuffles, 3.3 shared-memory
+// lane for row Y of instance g at word 30 j + 5 g + Y of its plane, the high
+// plane 160 words (a multiple of the 32 banks) after the low one, so the row
+// reads are at fixed offsets and both they and the scattered stores (whichever
+// plane each lane's word goes to) hit 30 distinct banks.  Per instance-round that is 2.7 shuffles, 3.3 shared-memory
 // accesses and about 9 other instructions, against 16 shuffles and about 20
 // others for the 25-lane form.
 //
@@ -24,6 +25,7 @@
 // so a state's first bytes are directly its squeezed output block.
 #pragma once
 #include "dil_keccak.cuh"
+#include "dil_ntt.cuh"
 
 namespace dil {
 
@@ -31,9 +33,45 @@ constexpr int K6_WORDS = 50;            // one state: 25 lanes x 2 words
 constexpr int K6_STATES = 6;
 constexpr int K6_PI_WORDS = 320;        // exchange buffer: two planes of 5 x 30 words, + read slack
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+// Per-lane constants of the six-state permutation, one word per slot j and a
+// word of shuffle sources, built at compile time:
+//   slot word: bits 0-10 byte offset in the exchange buffer of the slot's low
+//   word after rho (its high word in bits 11-21; the planes are swapped when
+//   the rotation is >= 32), bits 22-26 the rotation mod 32, bits 27-29 the
+//   column x held by the slot;
+//   source word: the lanes of rows y + 1 .. y + 4 of the instance, 5 bits each.
+// Read with coalesced cached loads (lanes ask for different words, which a
+// constant-memory table would serialise).
+struct K6Lanes {
+    uint32_t w[6][32];
+};
+
+namespace detail {
+constexpr int rho_c(int x, int y) {
+    constexpr int R[5][5] = {{0, 1, 62, 28, 27}, {36, 44, 6, 55, 20}, {3, 10, 43, 25, 39}, {41, 45, 15, 21, 8},
+                             {18, 2, 61, 56, 14}};
+    return R[y][x];
 }
+constexpr K6Lanes make_k6_lanes() {
+    K6Lanes t{};
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane < 30 ? lane / 5 : 5, y = lane < 30 ? lane % 5 : 4;
+        for (int j = 0; j < 5; ++j) {
+            const int x = (j + y) % 5, r = rho_c(x, y);
+            const int Y = (2 * x + 3 * y) % 5, jd = (y - Y + 5) % 5;
+            const uint32_t d = 4u * (30 * jd + 5 * g + Y);
+            const uint32_t lo = r >= 32 ? d + 640 : d, hi = r >= 32 ? d : d + 640;
+            t.w[j][lane] = lo | (hi << 11) | ((uint32_t)(r & 31) << 22) | ((uint32_t)x << 27);
+        }
+        uint32_t src = 0;
+        for (int k = 1; k < 5; ++k) src |= (uint32_t)(5 * g + (y + k) % 5) << (5 * (k - 1));
+        t.w[5][lane] = src;
+    }
+    return t;
+}
+}  // namespace detail
+
+static __device__ const K6Lanes c_k6_lanes = detail::make_k6_lanes();
 
 // Permutes the six states at shared address kst (300 words) using the
 // exchange buffer at shared address kpi (K6_PI_WORDS words).  Called by all 32
@@ -44,23 +82,21 @@ static __device__ __noinline__ void keccak6_permute_impl(uint32_t kst, uint32_t 
     const int g = on ? lane / 5 : 5;
     const int y = on ? lane - 5 * g : 4;
     // slot j of this lane holds state lane (x, y) with x = (j + y) mod 5
+    const uint32_t sw = __ldg(&c_k6_lanes.w[5][lane]);
     int src[4];   // lanes of rows y + 1 .. y + 4 of the same instance
 #pragma unroll
-    for (int k = 1; k < 5; ++k) src[k - 1] = 5 * g + (y + k) % 5;
+    for (int k = 0; k < 4; ++k) src[k] = (sw >> (5 * k)) & 31;
     const uint32_t row = kst + 4 * (K6_WORDS * g + 10 * y);
-    uint32_t a[10], dlo[5], dhi[5];
-    int rot[5];
+    uint32_t a[10], dlo[5], dhi[5], rot[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        const int x = (j + y) % 5;
-        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(a[2 * j]), "=r"(a[2 * j + 1]) : "r"(row + 8 * x));
-        const int r = rho_offset(x, y);
-        rot[j] = r & 31;
-        // pi: (x, y) -> (X, Y) = (y, 2x + 3y), which sits in slot (X - Y) mod 5 of lane Y
-        const int Y = (2 * x + 3 * y) % 5, jd = (y - Y + 5) % 5;
-        const uint32_t d = kpi + 4 * (30 * jd + 5 * g + Y);
-        dlo[j] = r >= 32 ? d + 600 : d;   // a rotation by >= 32 swaps the halves
-        dhi[j] = r >= 32 ? d : d + 600;
+        const uint32_t w = __ldg(&c_k6_lanes.w[j][lane]);
+        dlo[j] = kpi + (w & 0x7FFu);
+        dhi[j] = kpi + ((w >> 11) & 0x7FFu);
+        rot[j] = (w >> 22) & 31u;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(a[2 * j]), "=r"(a[2 * j + 1])
+                     : "r"(row + 8 * (w >> 27)));
     }
     const uint32_t rd = kpi + 4 * lane;
     const bool has00 = on && y == 0;
@@ -104,7 +140,7 @@ static __device__ __noinline__ void keccak6_permute_impl(uint32_t kst, uint32_t 
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             asm volatile("ld.shared.u32 %0, [%1];" : "=r"(b[2 * j]) : "r"(rd + 120 * j) : "memory");
-            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(b[2 * j + 1]) : "r"(rd + 600 + 120 * j) : "memory");
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(b[2 * j + 1]) : "r"(rd + 640 + 120 * j) : "memory");
         }
         __syncwarp();
         // chi along the row: slots j + 1, j + 2 hold columns x + 1, x + 2
@@ -122,8 +158,8 @@ static __device__ __noinline__ void keccak6_permute_impl(uint32_t kst, uint32_t 
     if (on) {
 #pragma unroll
         for (int j = 0; j < 5; ++j)
-            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(row + 8 * ((j + y) % 5)), "r"(a[2 * j]),
-                         "r"(a[2 * j + 1])
+            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(row + 8 * (__ldg(&c_k6_lanes.w[j][lane]) >> 27)),
+                         "r"(a[2 * j]), "r"(a[2 * j + 1])
                          : "memory");
     }
     __syncwarp();

@@ -78,9 +78,49 @@ __device__ __forceinline__ void gs_bfly(int32_t &a, int32_t &b, int32_t z) {
     b = mont_mul(z, t - b);
 }
 
-// Forward NTT.  In: L0, |r| < q.  Out: L2, |r| < 9q, unscaled.
-// zt: the forward twiddles in shared memory (per-lane indices).
-__device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_t *zt, int lane) {
+// Shared-memory accesses by 32-bit shared-window address (the out-of-line
+// transforms receive addresses, not generic pointers).  Exchange-buffer
+// accesses are ordered (volatile, memory clobber); twiddle loads read
+// constant data and may be scheduled freely.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void sts32(uint32_t a, int32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ int32_t lds32(uint32_t a) {
+    int32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ldz32(uint32_t a) {
+    int32_t v;
+    asm("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int2 ldz64(uint32_t a) {
+    int2 v;
+    asm("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int4 ldz128(uint32_t a) {
+    int4 v;
+    asm("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// Eight coefficients of one lane, passed by value to the out-of-line transforms.
+struct Poly8 {
+    int32_t v[8];
+};
+
+// Forward NTT.  In: L0, |r| < q.  Out: L2, |r| < 9q, unscaled.  buf: the
+// warp's exchange buffer (288 words), zt: the forward twiddles (shared).
+// Out of line: one copy of the code serves every call site, which keeps the
+// fused kernels' instruction footprint small.
+static __device__ __noinline__ Poly8 ntt_fwd_impl(Poly8 p, uint32_t buf, uint32_t zt) {
+    const int lane = threadIdx.x & 31;
+    int32_t *r = p.v;
     // level 1 (len 128): pairs (m, m+4)
     {
         const int32_t z = c_zetas.z[1];
@@ -99,21 +139,22 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
     ct_bfly(r[6], r[7], c_zetas.z[7]);
     // exchange L0 -> L1
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[lane + 36 * m] = r[m];
+    for (int m = 0; m < 8; ++m) sts32(buf + 4 * (lane + 36 * m), r[m]);
     __syncwarp();
-    const int b = lane >> 2, base1 = 36 * (lane >> 2) + (lane & 3);
+    const int b = lane >> 2;
+    const uint32_t base1 = buf + 4 * (36 * b + (lane & 3));
 #pragma unroll
-    for (int m = 0; m < 8; ++m) r[m] = buf[base1 + 4 * m];
+    for (int m = 0; m < 8; ++m) r[m] = lds32(base1 + 16 * m);
     __syncwarp();
     // level 4 (len 16): pairs (m, m+4), twiddle 8 + b
     {
-        const int32_t z = zt[8 + b];
+        const int32_t z = ldz32(zt + 4 * (8 + b));
 #pragma unroll
         for (int m = 0; m < 4; ++m) ct_bfly(r[m], r[m + 4], z);
     }
     // level 5 (len 8): pairs (m, m+2), twiddles 16 + 2b + {0, 1}
     {
-        const int2 z = *reinterpret_cast<const int2 *>(zt + 16 + 2 * b);
+        const int2 z = ldz64(zt + 4 * (16 + 2 * b));
         ct_bfly(r[0], r[2], z.x);
         ct_bfly(r[1], r[3], z.x);
         ct_bfly(r[4], r[6], z.y);
@@ -121,7 +162,7 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
     }
     // level 6 (len 4): pairs (m, m+1), twiddles 32 + 4b + {0..3}
     {
-        const int4 z = *reinterpret_cast<const int4 *>(zt + 32 + 4 * b);
+        const int4 z = ldz128(zt + 4 * (32 + 4 * b));
         ct_bfly(r[0], r[1], z.x);
         ct_bfly(r[2], r[3], z.y);
         ct_bfly(r[4], r[5], z.z);
@@ -129,15 +170,15 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
     }
     // exchange L1 -> L2
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[base1 + 4 * m + (m >> 1)] = r[m];
+    for (int m = 0; m < 8; ++m) sts32(base1 + 4 * (4 * m + (m >> 1)), r[m]);
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) r[m] = buf[9 * lane + m];
+    for (int m = 0; m < 8; ++m) r[m] = lds32(buf + 4 * (9 * lane + m));
     __syncwarp();
     // level 7 (len 2): pairs (m, m+2), twiddles 64 + 2t + {0, 1} (one 8-byte
     // load per lane: a half-warp reads 128 contiguous bytes, conflict-free)
     {
-        const int2 z = *reinterpret_cast<const int2 *>(zt + 64 + 2 * lane);
+        const int2 z = ldz64(zt + 4 * (64 + 2 * lane));
         ct_bfly(r[0], r[2], z.x);
         ct_bfly(r[1], r[3], z.x);
         ct_bfly(r[4], r[6], z.y);
@@ -145,21 +186,24 @@ __device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_
     }
     // level 8 (len 1): pairs (m, m+1), twiddles 128 + 4t + {0..3} (16-byte load)
     {
-        const int4 z = *reinterpret_cast<const int4 *>(zt + 128 + 4 * lane);
+        const int4 z = ldz128(zt + 4 * (128 + 4 * lane));
         ct_bfly(r[0], r[1], z.x);
         ct_bfly(r[2], r[3], z.y);
         ct_bfly(r[4], r[5], z.z);
         ct_bfly(r[6], r[7], z.w);
     }
+    return p;
 }
 
 // Inverse NTT.  In: L2, |r| < q.  Out: L0, |r| < q, equal to INTT(in) * 2^32,
 // so it turns pointwise Montgomery products into plain coefficients.
 // izt: the inverse twiddles in shared memory.
-__device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_t *izt, int lane) {
+static __device__ __noinline__ Poly8 ntt_inv_impl(Poly8 p, uint32_t buf, uint32_t izt) {
+    const int lane = threadIdx.x & 31;
+    int32_t *r = p.v;
     // len 1: pairs (m, m+1), twiddles 128 + 4t + {0..3}
     {
-        const int4 z = *reinterpret_cast<const int4 *>(izt + 128 + 4 * lane);
+        const int4 z = ldz128(izt + 4 * (128 + 4 * lane));
         gs_bfly(r[0], r[1], z.x);
         gs_bfly(r[2], r[3], z.y);
         gs_bfly(r[4], r[5], z.z);
@@ -167,7 +211,7 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
     }
     // len 2: pairs (m, m+2), twiddles 64 + 2t + {0, 1}
     {
-        const int2 z = *reinterpret_cast<const int2 *>(izt + 64 + 2 * lane);
+        const int2 z = ldz64(izt + 4 * (64 + 2 * lane));
         gs_bfly(r[0], r[2], z.x);
         gs_bfly(r[1], r[3], z.x);
         gs_bfly(r[4], r[6], z.y);
@@ -175,15 +219,16 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
     }
     // exchange L2 -> L1
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[9 * lane + m] = r[m];
+    for (int m = 0; m < 8; ++m) sts32(buf + 4 * (9 * lane + m), r[m]);
     __syncwarp();
-    const int b = lane >> 2, base1 = 36 * (lane >> 2) + (lane & 3);
+    const int b = lane >> 2;
+    const uint32_t base1 = buf + 4 * (36 * b + (lane & 3));
 #pragma unroll
-    for (int m = 0; m < 8; ++m) r[m] = buf[base1 + 4 * m + (m >> 1)];
+    for (int m = 0; m < 8; ++m) r[m] = lds32(base1 + 4 * (4 * m + (m >> 1)));
     __syncwarp();
     // len 4: pairs (m, m+1), twiddles 32 + 4b + {0..3}
     {
-        const int4 z = *reinterpret_cast<const int4 *>(izt + 32 + 4 * b);
+        const int4 z = ldz128(izt + 4 * (32 + 4 * b));
         gs_bfly(r[0], r[1], z.x);
         gs_bfly(r[2], r[3], z.y);
         gs_bfly(r[4], r[5], z.z);
@@ -191,7 +236,7 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
     }
     // len 8: pairs (m, m+2), twiddles 16 + 2b + {0, 1}
     {
-        const int2 z = *reinterpret_cast<const int2 *>(izt + 16 + 2 * b);
+        const int2 z = ldz64(izt + 4 * (16 + 2 * b));
         gs_bfly(r[0], r[2], z.x);
         gs_bfly(r[1], r[3], z.x);
         gs_bfly(r[4], r[6], z.y);
@@ -199,16 +244,16 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
     }
     // len 16: pairs (m, m+4), twiddle 8 + b
     {
-        const int32_t z = izt[8 + b];
+        const int32_t z = ldz32(izt + 4 * (8 + b));
 #pragma unroll
         for (int m = 0; m < 4; ++m) gs_bfly(r[m], r[m + 4], z);
     }
     // exchange L1 -> L0
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[base1 + 4 * m] = r[m];
+    for (int m = 0; m < 8; ++m) sts32(base1 + 16 * m, r[m]);
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) r[m] = buf[lane + 36 * m];
+    for (int m = 0; m < 8; ++m) r[m] = lds32(buf + 4 * (lane + 36 * m));
     __syncwarp();
     // len 32: pairs (m, m+1), twiddle 4 + m/2
     gs_bfly(r[0], r[1], c_zetas.iz[4]);
@@ -227,6 +272,27 @@ __device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_
         r[m] = mont_mul(NTT_F, a + c);
         r[m + 4] = mont_mul(NTT_G, a - c);
     }
+    return p;
+}
+
+__device__ __forceinline__ void ntt_fwd(int32_t r[8], int32_t *buf, const int32_t *zt, int lane) {
+    (void)lane;
+    Poly8 p;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p.v[m] = r[m];
+    p = ntt_fwd_impl(p, smem_addr(buf), smem_addr(zt));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = p.v[m];
+}
+
+__device__ __forceinline__ void ntt_inv(int32_t r[8], int32_t *buf, const int32_t *izt, int lane) {
+    (void)lane;
+    Poly8 p;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p.v[m] = r[m];
+    p = ntt_inv_impl(p, smem_addr(buf), smem_addr(izt));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = p.v[m];
 }
 
 // Loads the twiddle tables into shared memory (whole block participates).

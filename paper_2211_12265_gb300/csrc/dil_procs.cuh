@@ -203,6 +203,7 @@ __device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi
         const int c = min(K6_STATES, hi - j);
         expand_mask_six<V::ZBITS, V::GAMMA1>(rhop, kappa + j, c, y + j * N, ws.kst, ws.kpi(), ws.win, lane);
         __syncwarp();
+#pragma unroll 1
         for (int u = j; u < j + c; ++u) {
             load_l0(r, y + u * N, lane);
             ntt_fwd(r, ws.buf, zt, lane);
@@ -233,6 +234,7 @@ __device__ __forceinline__ void accumulate_row(int32_t acc[8], const int32_t *ah
     int32_t a[8], v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = 0;
+#pragma unroll 1
     for (int j = 0; j < l; ++j) {
         load_l2_cg(a, ahat + j * N, lane);
         load_l2(v, vhat + j * N, lane);
@@ -279,6 +281,7 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
     group_sync<P>(bar);
     // s1: sample, pack into sk, NTT  (l.4)
     constexpr int U1 = Units<V::L, P>::SIZE;
+#pragma unroll 1
     for (int j = U1 * g; j < V::L; j += U1 * P) {
         const bool two = U1 == 2 && j + 1 < V::L;
         if (two)
@@ -302,6 +305,7 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
     expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
     group_sync<P>(bar);
     // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)  (l.3, l.5, l.6)
+#pragma unroll 1
     for (int i = g; i < V::K; i += P) {
         accumulate_row(acc, scratch + (V::L + i * V::L) * N, V::L, scratch, lane);
 #pragma unroll
@@ -374,6 +378,7 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
     constexpr int KL = V::K * V::L;
     expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, ws, lane);
     // s^1, s^2, t^0  (l.4): polynomials u = 0 .. l + 2k - 1 across the group
+#pragma unroll 1
     for (int u = g; u < V::L + 2 * V::K; u += P) {
         if (u < V::L) {
             unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S1 + u * V::POLYETA, V::ETA, ws, lane);
@@ -424,6 +429,7 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
     expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), key + S::AH * N, ws, lane);
     // s^1, s^2, t^0 (when the secret key is resident) and NTT(t1 2^d)
     const int first = sk ? 0 : V::L + 2 * V::K;
+#pragma unroll 1
     for (int u = first + g; u < V::L + 3 * V::K; u += P) {
         if (u < V::L) {
             unpack_poly_l0<V::ETABITS>(r, sk + V::SK_S1 + u * V::POLYETA, V::ETA, ws, lane);
@@ -467,9 +473,11 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
                              itr + S::YH * N, ws, zt, lane);
     group_sync<P>(bar);
     // w = INTT(A^ o y^); w1 = HighBits(w)  (l.7-8)
+#pragma unroll 1
     for (int i = g; i < V::K; i += P) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = 0;
+#pragma unroll 1
         for (int j = 0; j < V::L; ++j) {
             load_l2_cg(a, pre + (S::AH + i * V::L + j) * N, lane);
             load_l2(r, itr + (S::YH + j) * N, lane);
@@ -503,6 +511,7 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
     // c^ = NTT(SampleInBall(c~))  (l.10)
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta  (l.11, l.14)
+#pragma unroll 1
     for (int j = g; j < V::L && !*vflag; j += P) {
         load_l2_cg(a, pre + (S::S1H + j) * N, lane);
 #pragma unroll
@@ -522,6 +531,7 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
         store_l0(itr + (S::Z + j) * N, r, lane);
     }
     // v_s = INTT(c^ o s^2); r0 = LowBits(w - v_s)  (l.12-14)
+#pragma unroll 1
     for (int i = g; i < V::K && !*vflag; i += P) {
         load_l2_cg(a, pre + (S::S2H + i) * N, lane);
 #pragma unroll
@@ -548,6 +558,7 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
     group_sync<P>(bar);
     if (*vflag) return false;
     // v_t = INTT(c^ o t^0); h = MakeHint(-v_t, w - v_s + v_t)  (l.17-19)
+#pragma unroll 1
     for (int i = g; i < V::K && !*vflag; i += P) {
         load_l2_cg(a, pre + (S::T0H + i) * N, lane);
 #pragma unroll
@@ -587,6 +598,7 @@ template <int LEVEL, int P>
 __device__ void sign_pack(uint8_t *sig, const int32_t *itr, const GroupSmem &gs, int g, int lane) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
+#pragma unroll 1
     for (int j = g; j < V::L; j += P) {
         int32_t v[8];
         load_l2(v, itr + (S::Z + j) * N, lane);   // 8 consecutive coefficients
@@ -596,6 +608,7 @@ __device__ void sign_pack(uint8_t *sig, const int32_t *itr, const GroupSmem &gs,
     sig[lane] = gs.ctilde[lane];
     uint8_t *h = sig + V::SIG_H;
     int base = 0;
+#pragma unroll 1
     for (int i = 0; i < V::K; ++i) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -637,6 +650,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         __syncwarp();
         bool bad = false;
         int prev = 0;
+#pragma unroll 1
         for (int i = 0; i < V::K; ++i) {
             int end = ws.sq[V::OMEGA + i];
             if (end < prev || end > V::OMEGA) {
@@ -659,6 +673,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     group_sync<P>(bar);
     if (*vflag) return 0;
     // z: unpack, ||z|| < gamma1 - beta, z^ = NTT(z)  (Alg 3 l.6 first term, l.4)
+#pragma unroll 1
     for (int j = g; j < V::L && !*vflag; j += P) {
         unpack_poly_l0<V::ZBITS>(r, sig + V::SIG_Z + j * V::POLYZ, V::GAMMA1, ws, lane);
         bool b = false;
@@ -697,6 +712,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)  (l.4-5)
     using S = Scratch<LEVEL>;
     const int32_t *ahat = KEYED ? key + S::AH * N : scratch + V::L * N;
+#pragma unroll 1
     for (int i = g; i < V::K; i += P) {
         accumulate_row(acc, ahat + i * V::L * N, V::L, scratch, lane);
         if (KEYED) {

@@ -52,6 +52,7 @@ __device__ __forceinline__ void expand_a_poly(const uint8_t *rho, int i, int j, 
     uint32_t lo, hi;
     absorb_seed(lo, hi, rho, 4, (uint32_t)j | ((uint32_t)i << 8), 2, 168, lane);
     int ctr = 0;
+#pragma unroll 1
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo, hi, sq, 21, lane);
         __syncwarp();
@@ -70,6 +71,7 @@ __device__ __forceinline__ void expand_a_pair(const uint8_t *rho, int i0, int j0
     seed_words(lo1, hi1, rho, 4, (uint32_t)j1 | ((uint32_t)i1 << 8), 2, 168, lane);
     keccak_f2(lo0, hi0, lo1, hi1);
     int c0 = 0, c1 = 0;
+#pragma unroll 1
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo0, hi0, sq0, 21, lane);
         squeeze_words(lo1, hi1, sq1, 21, lane);
@@ -94,33 +96,29 @@ __device__ __forceinline__ void expand_a_six(const uint8_t *rho, int p0, int cou
         [&](int g) { const int p = p0 + g; return (uint32_t)(p % L) | ((uint32_t)(p / L) << 8) | (0x1Fu << 16); },
         count, 168, lane);
     keccak6_permute(kst, kpi);
-    int ctr[K6_STATES];
-#pragma unroll
-    for (int g = 0; g < K6_STATES; ++g) ctr[g] = 0;
+    int mine = 0;   // lane g < count: coefficients accepted so far for instance g
+#pragma unroll 1
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
-        bool more = false;
+#pragma unroll 1
+        for (int g = 0; g < count; ++g) {
+            int c = __shfl_sync(FULL, mine, g);
+            if (c >= N) continue;
+            const uint8_t *sq = reinterpret_cast<const uint8_t *>(kst + K6_WORDS * g);
+            int32_t *dst = out + g * N;
 #pragma unroll
-        for (int g = 0; g < K6_STATES; ++g) {
-            if (g < count && ctr[g] < N) {
-                const uint8_t *sq = reinterpret_cast<const uint8_t *>(kst + K6_WORDS * g);
-                int32_t *dst = out + g * N;
-                int c = ctr[g];
-#pragma unroll
-                for (int rnd = 0; rnd < 2; ++rnd) {
-                    const int k = rnd * 32 + lane;
-                    const bool valid = k < 56;
-                    const uint32_t v = valid ? (get_field(sq, 24 * k, 24) & 0x7FFFFFu) : 0u;
-                    const bool acc = valid && v < (uint32_t)Q;
-                    const uint32_t mask = __ballot_sync(FULL, acc);
-                    const int pos = c + __popc(mask & lanemask_lt(lane));
-                    if (acc && pos < N) dst[pos] = (int32_t)v;
-                    c += __popc(mask);
-                }
-                ctr[g] = c;
-                more |= c < N;
+            for (int rnd = 0; rnd < 2; ++rnd) {
+                const int k = rnd * 32 + lane;
+                const bool valid = k < 56;
+                const uint32_t v = valid ? (get_field(sq, 24 * k, 24) & 0x7FFFFFu) : 0u;
+                const bool acc = valid && v < (uint32_t)Q;
+                const uint32_t mask = __ballot_sync(FULL, acc);
+                const int pos = c + __popc(mask & lanemask_lt(lane));
+                if (acc && pos < N) dst[pos] = (int32_t)v;
+                c += __popc(mask);
             }
+            if (lane == g) mine = c;
         }
-        if (!more) break;
+        if (!__any_sync(FULL, lane < count && mine < N)) break;
         keccak6_permute(kst, kpi);
     }
 }
@@ -152,6 +150,7 @@ __device__ __forceinline__ void expand_mask_six(const uint8_t *rhop, int nonce0,
         __syncwarp();
         const int c_lo = (1088 * b) / ZBITS;
         const int c_hi = min(N, (1088 * (b + 1)) / ZBITS);
+#pragma unroll 1
         for (int g = 0; g < count; ++g) {
             const uint8_t *wb = reinterpret_cast<const uint8_t *>(win + 38 * g);
             for (int c = c_lo + lane; c < c_hi; c += 32)
@@ -192,6 +191,7 @@ __device__ __forceinline__ void expand_s_poly(const uint8_t *rhop, int nonce, in
     uint32_t lo, hi;
     absorb_seed(lo, hi, rhop, 8, (uint32_t)nonce & 0xFFFFu, 2, 136, lane);
     int ctr = 0;
+#pragma unroll 1
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo, hi, sq, 17, lane);
         __syncwarp();
@@ -210,6 +210,7 @@ __device__ __forceinline__ void expand_s_pair(const uint8_t *rhop, int nonce0, i
     seed_words(lo1, hi1, rhop, 8, (uint32_t)nonce1 & 0xFFFFu, 2, 136, lane);
     keccak_f2(lo0, hi0, lo1, hi1);
     int c0 = 0, c1 = 0;
+#pragma unroll 1
     for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
         squeeze_words(lo0, hi0, sq0, 17, lane);
         squeeze_words(lo1, hi1, sq1, 17, lane);
@@ -282,6 +283,7 @@ __device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *b
     __syncwarp();
     uint64_t signs = *reinterpret_cast<const unsigned long long *>(sq);
     int pos = 8, blocks = 1;
+#pragma unroll 1
     for (int i = N - TAU; i < N; ++i) {
         int b;
         do {
