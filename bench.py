@@ -323,6 +323,8 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     shfl_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["shfl"])
     peak = SMS * lop3_rate * SM_MAX_MHZ * 1e6 / 1e12
     traffic = load_traffic(level, n)
+    table = autotune.load() or {}
+    sign_p = table.get("plain", {}).get(str(level), {}).get("sign", {}).get("warps_per_task", 2)
 
     res = {
         "metric": METRIC,
@@ -356,7 +358,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": 2 * args.steps,
         "gpu_launches_note": "plain timed region: one Sign and one Verify kernel per step",
-        "roofline": {"bound": "alu", "kernel": f"k_sign<{level}>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": f"k_sign<{level}, {sign_p}>", "achieved": achieved,
                      "peak": peak, "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
                      "traffic": traffic, "ops_per_sign": ops / n,
                      "peak_basis": f"{SMS} SMs x {lop3_rate:.1f} LOP3 thread-ops/SM/clk (measured live) x "

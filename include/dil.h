@@ -105,7 +105,7 @@ int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8
  * dil_sign without a context; runs on the current device with the default
  * repetition cap.  Scratch is a 64 MiB array inside the library's device image
  * (held by every GPU that loads the library until exit), so n may not exceed
- * 1489 / 963 / 606 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
+ * 1337 / 897 / 579 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
  * The first call on a device looks up the array's address (cudaGetSymbolAddress)
  * and should come before any stream capture.  All calls share the array: calls
  * that overlap on the GPU race and must be serialised.  Nothing in it needs

@@ -20,9 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuning_gb300.json")
 
 PLAIN_SHAPES = [(1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2), (4, 4), (8, 4)]
-PERSIST_SHAPES = [(2, 1, 0, 1, 0), (2, 1, 0, 1, 4), (4, 1, 0, 1, 0), (4, 1, 0, 1, 4), (8, 1, 0, 1, 0),
-                  (8, 1, 0, 1, 4), (8, 1, 0, 2, 4), (8, 2, 0, 1, 4), (8, 2, 0, 1, 8), (8, 2, 0, 1, 0),
-                  (8, 4, 0, 1, 4), (8, 4, 0, 1, 8)]
+PERSIST_SHAPES = [(4, 1, 0, 1, 4), (8, 1, 0, 1, 0), (8, 1, 0, 1, 4), (8, 1, 0, 1, 8), (8, 1, 0, 1, 16),
+                  (8, 1, 0, 2, 8), (8, 2, 0, 1, 4), (8, 2, 0, 1, 8), (8, 4, 0, 1, 4), (8, 4, 0, 1, 8)]
 OPS = {"keygen": 0, "sign": 1, "verify": 2}
 
 

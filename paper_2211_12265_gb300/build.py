@@ -39,7 +39,7 @@ def _deps() -> list[str]:
     return out
 
 
-def source_digest(unit: str = "dil_ops.cu") -> str:
+def source_digest(unit: str = "dil_sign.cu") -> str:
     """SHA-256 over one kernel translation unit and the device headers it
     includes (ties a committed profile to the kernel version it measured)."""
     import hashlib

@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(256, 4) k_sign_keyed(int n, int n_keys, const 
     sign_prepare_keyed<LEVEL, P>(sk + (size_t)key * V::SK, msg + m0, (size_t)(m1 - m0), *v.gs, v.g, v.bar, v.lane);
     int it = 0;
     bool ok = false;
+    MaskStream ms{0, 0};
     while (it < max_iter) {
-        ok = sign_attempt<LEVEL, P>(it * V::L, pre, itr, *v.gs, *v.ws, v.zt, v.izt, v.g, v.bar, v.lane);
+        ok = sign_attempt<LEVEL, P>(it * V::L, pre, itr, ms, *v.gs, *v.ws, v.zt, v.izt, v.g, v.bar, v.lane);
         ++it;
         if (ok) break;
     }

@@ -116,6 +116,7 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
                                 const int32_t *izt, int g, int bar, int lane) {
     const int cap = iter_cap<LEVEL>(pc.max_iter_override);
     const bool leader = g == 0 && lane == 0;
+    MaskStream ms{0, 0};
     for (;;) {
         if (leader) {
             const int r = atomicAdd(&tk.next_r, 1);
@@ -126,7 +127,7 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
         const int r = *(volatile int *)&gs.claim2;
         group_sync<P>(bar);
         if (r < 0) break;
-        if (sign_attempt<LEVEL, P>(Lv<LEVEL>::L * r, pre, itr, gs, ws, zt, izt, g, bar, lane)) {
+        if (sign_attempt<LEVEL, P>(Lv<LEVEL>::L * r, pre, itr, ms, gs, ws, zt, izt, g, bar, lane)) {
             commit<LEVEL, P>(pc, tk, r, jb, local, itr, gs, g, bar, lane);
             break;
         }

@@ -108,8 +108,9 @@ __global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *ka
     }
     while (V::L - j >= 3 || (j == 0 && V::L > 0)) {
         const int c = min(K6_STATES, V::L - j);
-        expand_mask_six<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + j, c, o + j * N, ws.kst, ws.kpi(), ws.win,
-                                             lane);
+        int32_t *base = o + j * N;
+        expand_mask_six<V::ZBITS, V::GAMMA1>(
+            gs.rhop, kappa[item] + j, c, [&](int g) { return base + g * N; }, ws.kst, ws.kpi(), ws.win, lane);
         j += c;
     }
     for (; j < V::L; ++j) {

@@ -145,9 +145,12 @@ template <int LEVEL> struct Scratch {
     static constexpr int S2H = S1H + V::L;
     static constexpr int T0H = S2H + V::K;
     static constexpr int PRE_POLYS = T0H + V::K;
-    // offsets inside the per-repetition part
+    // offsets inside the per-repetition part; y is a ring of YRING
+    // polynomials indexed by nonce (a worker samples masks six nonces at a
+    // time and keeps the ones the next repetition needs)
     static constexpr int Y = 0;
-    static constexpr int YH = Y + V::L;
+    static constexpr int YRING = V::L + K6_STATES - 1;
+    static constexpr int YH = Y + YRING;
     static constexpr int W = YH + V::L;
     static constexpr int Z = W + V::K;
     static constexpr int ITR_POLYS = Z + V::L;
@@ -191,21 +194,29 @@ __device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out,
     __syncwarp();
 }
 
-// y_j = ExpandMask(rho', kappa + j) in coefficient order to y + j N and
-// y^_j = NTT(y_j) in index order to yh + j N, for j in [lo, hi).
+// Slot of nonce u's mask polynomial y (coefficient order) in the ring.
 template <int LEVEL>
-__device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi, int32_t *y, int32_t *yh,
+__device__ __forceinline__ int32_t *y_slot(int32_t *ring, int u) {
+    return ring + (u % Scratch<LEVEL>::YRING) * N;
+}
+
+// y_j = ExpandMask(rho', kappa + j) into its ring slot and y^_j = NTT(y_j) in
+// index order to yh + j N, for j in [lo, hi) (one warp's share of a
+// repetition when a task group has several warps).
+template <int LEVEL>
+__device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi, int32_t *ring, int32_t *yh,
                                   WarpSmem &ws, const int32_t *zt, int lane) {
     using V = Lv<LEVEL>;
     int32_t r[8], a[8];
     int j = lo;
     while (hi - j >= 3) {
-        const int c = min(K6_STATES, hi - j);
-        expand_mask_six<V::ZBITS, V::GAMMA1>(rhop, kappa + j, c, y + j * N, ws.kst, ws.kpi(), ws.win, lane);
+        const int c = min(K6_STATES, hi - j), u0 = kappa + j;
+        expand_mask_six<V::ZBITS, V::GAMMA1>(
+            rhop, u0, c, [&](int g) { return y_slot<LEVEL>(ring, u0 + g); }, ws.kst, ws.kpi(), ws.win, lane);
         __syncwarp();
 #pragma unroll 1
         for (int u = j; u < j + c; ++u) {
-            load_l0(r, y + u * N, lane);
+            load_l0(r, y_slot<LEVEL>(ring, kappa + u), lane);
             ntt_fwd(r, ws.buf, zt, lane);
             store_l2(yh + u * N, r, lane);
         }
@@ -213,14 +224,46 @@ __device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi
     }
     if (hi - j == 2) {
         expand_mask_pair<V::ZBITS, V::GAMMA1>(rhop, kappa + j, kappa + j + 1, r, a, ws.sq, ws.sq2, lane);
-        store_l0(y + (j + 1) * N, a, lane);
+        store_l0(y_slot<LEVEL>(ring, kappa + j + 1), a, lane);
         ntt_fwd(a, ws.buf, zt, lane);
         store_l2(yh + (j + 1) * N, a, lane);
     } else if (hi - j == 1) {
         expand_mask_poly<V::ZBITS, V::GAMMA1>(rhop, kappa + j, r, ws.sq, lane);
     }
     if (hi - j >= 1) {
-        store_l0(y + j * N, r, lane);
+        store_l0(y_slot<LEVEL>(ring, kappa + j), r, lane);
+        ntt_fwd(r, ws.buf, zt, lane);
+        store_l2(yh + j * N, r, lane);
+    }
+}
+
+// A worker's stream of masks: the ring holds y for nonces [lo, hi).
+struct MaskStream {
+    int lo, hi;
+};
+
+// One-warp form: y for nonces [kappa, kappa + l) from the stream, which
+// samples six consecutive nonces at a time, so the leftovers of one
+// repetition serve the next (a repetition that does not continue the stream
+// restarts it at kappa); y^ into yh.
+template <int LEVEL>
+__device__ void mask_stream(const uint8_t *rhop, int kappa, MaskStream &ms, int32_t *ring, int32_t *yh,
+                            WarpSmem &ws, const int32_t *zt, int lane) {
+    using V = Lv<LEVEL>;
+    if (kappa < ms.lo || kappa > ms.hi) ms.hi = kappa;
+    ms.lo = kappa;
+    while (ms.hi < kappa + V::L) {   // live nonces stay within [kappa, kappa + YRING)
+        const int u0 = ms.hi;
+        expand_mask_six<V::ZBITS, V::GAMMA1>(
+            rhop, u0, K6_STATES, [&](int g) { return y_slot<LEVEL>(ring, u0 + g); }, ws.kst, ws.kpi(), ws.win,
+            lane);
+        ms.hi += K6_STATES;
+    }
+    __syncwarp();
+    int32_t r[8];
+#pragma unroll 1
+    for (int j = 0; j < V::L; ++j) {
+        load_l0(r, y_slot<LEVEL>(ring, kappa + j), lane);
         ntt_fwd(r, ws.buf, zt, lane);
         store_l2(yh + j * N, r, lane);
     }
@@ -462,15 +505,18 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
 // pre: the task's precomputation part (possibly prepared by another warp
 // group, so it is read through L2); itr: this worker's per-repetition part.
 template <int LEVEL, int P>
-__device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws,
-                             const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
+__device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
+                             WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     volatile int *vflag = &gs.flag;
     int32_t r[8], a[8], acc[8], ch[8];
     // y = ExpandMask(rho', kappa); y^ = NTT(y)  (l.6)
-    expand_mask_range<LEVEL>(gs.rhop, kappa, share_lo<V::L, P>(g), share_lo<V::L, P>(g + 1), itr + S::Y * N,
-                             itr + S::YH * N, ws, zt, lane);
+    if constexpr (P == 1)
+        mask_stream<LEVEL>(gs.rhop, kappa, ms, itr + S::Y * N, itr + S::YH * N, ws, zt, lane);
+    else
+        expand_mask_range<LEVEL>(gs.rhop, kappa, share_lo<V::L, P>(g), share_lo<V::L, P>(g + 1), itr + S::Y * N,
+                                 itr + S::YH * N, ws, zt, lane);
     group_sync<P>(bar);
     // w = INTT(A^ o y^); w1 = HighBits(w)  (l.7-8)
 #pragma unroll 1
@@ -517,7 +563,7 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, GroupS
 #pragma unroll
         for (int m = 0; m < 8; ++m) r[m] = mont_mul(ch[m], a[m]);
         ntt_inv(r, ws.buf, izt, lane);
-        load_l0(a, itr + (S::Y + j) * N, lane);
+        load_l0(a, y_slot<LEVEL>(itr + S::Y * N, kappa + j), lane);
         bool bad = false;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {

@@ -123,13 +123,14 @@ __device__ __forceinline__ void expand_a_six(const uint8_t *rho, int p0, int cou
     }
 }
 
-// Six-instance ExpandMask: y_j for nonces nonce0 .. nonce0 + count - 1
-// (count <= 6), coefficient c of y_j at out[j 256 + c] (natural order).
-// After each permutation the 136-byte block is copied behind the last 8 bytes
-// of the previous one into a per-instance window (win: 6 x 38 words), and the
-// fields whose last bit lies in this block are extracted.
-template <int ZBITS, int32_t GAMMA1>
-__device__ __forceinline__ void expand_mask_six(const uint8_t *rhop, int nonce0, int count, int32_t *out,
+// Six-instance ExpandMask: y for nonces nonce0 .. nonce0 + count - 1
+// (count <= 6), coefficient c of instance g's polynomial at dst(g)[c]
+// (natural order).  After each permutation the 136-byte block is copied
+// behind the last 8 bytes of the previous one into a per-instance window
+// (win: 6 x 38 words), and the fields whose last bit lies in this block are
+// extracted.
+template <int ZBITS, int32_t GAMMA1, class Dst>
+__device__ __forceinline__ void expand_mask_six(const uint8_t *rhop, int nonce0, int count, Dst dst,
                                                 uint32_t *kst, uint32_t *kpi, uint32_t *win, int lane) {
     keccak6_seed(
         kst, reinterpret_cast<const uint32_t *>(rhop), 16,
@@ -153,8 +154,9 @@ __device__ __forceinline__ void expand_mask_six(const uint8_t *rhop, int nonce0,
 #pragma unroll 1
         for (int g = 0; g < count; ++g) {
             const uint8_t *wb = reinterpret_cast<const uint8_t *>(win + 38 * g);
+            int32_t *out = dst(g);
             for (int c = c_lo + lane; c < c_hi; c += 32)
-                out[g * N + c] = GAMMA1 - (int32_t)get_field(wb, ZBITS * c - (1088 * b - 64), ZBITS);
+                out[c] = GAMMA1 - (int32_t)get_field(wb, ZBITS * c - (1088 * b - 64), ZBITS);
         }
         __syncwarp();
     }

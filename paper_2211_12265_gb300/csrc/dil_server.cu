@@ -31,7 +31,12 @@ double now_s() { return std::chrono::duration<double>(Clock::now().time_since_ep
 
 constexpr int MAX_SIG = 4595;
 constexpr size_t POLY = 256 * sizeof(int32_t);
-constexpr size_t MAX_TASK_POLYS = 29;   // keyed Sign scratch of level 5 (largest of all keyed tasks)
+// Scratch polynomials of the largest keyed task (Sign or Verify, any level).
+size_t max_task_polys() {
+    size_t m = 0;
+    for (int level : {2, 3, 5}) m = std::max({m, dil::keyed_sign_polys(level), dil::keyed_verify_polys(level)});
+    return m;
+}
 
 int level_slot(int level) { return level == 2 ? 0 : level == 3 ? 1 : level == 5 ? 2 : -1; }
 size_t sig_bytes(int level) { return level == 2 ? 2420 : level == 3 ? 3293 : 4595; }
@@ -118,7 +123,7 @@ bool alloc_slot(Slot &s, int max_batch, size_t msg_cap) {
               cudaMalloc(&s.d_sig_out, n * MAX_SIG) == cudaSuccess && cudaMalloc(&s.d_ok, n) == cudaSuccess &&
               cudaMalloc(&s.d_off, offs * 8) == cudaSuccess && cudaMalloc(&s.d_key, n * 4) == cudaSuccess &&
               cudaMalloc(&s.d_status, n * 4) == cudaSuccess &&
-              cudaMalloc(&s.d_scratch, n * MAX_TASK_POLYS * POLY) == cudaSuccess &&
+              cudaMalloc(&s.d_scratch, n * max_task_polys() * POLY) == cudaSuccess &&
               cudaMallocHost(&s.h_msg, msg_cap + 16) == cudaSuccess &&
               cudaMallocHost(&s.h_sig_in, n * MAX_SIG) == cudaSuccess &&
               cudaMallocHost(&s.h_sig_out, n * MAX_SIG) == cudaSuccess && cudaMallocHost(&s.h_ok, n) == cudaSuccess &&
@@ -130,7 +135,7 @@ bool alloc_slot(Slot &s, int max_batch, size_t msg_cap) {
 
 size_t slot_device_bytes(int max_batch, size_t msg_cap) {
     const size_t n = (size_t)max_batch;
-    return msg_cap + 16 + 2 * n * MAX_SIG + n + (n + 6) * 8 + 8 * n + n * MAX_TASK_POLYS * POLY;
+    return msg_cap + 16 + 2 * n * MAX_SIG + n + (n + 6) * 8 + 8 * n + n * max_task_polys() * POLY;
 }
 
 void finish_request(dil_server *sv, Req *r, double t) {
@@ -190,7 +195,7 @@ bool dispatch(dil_server *sv, Slot &s) {
     for (auto &g : s.groups) {
         const int li = level_slot(g.level);
         dil_keystore *ks = sv->ks[li];
-        int32_t *scratch = s.d_scratch + (size_t)g.first * MAX_TASK_POLYS * 256;
+        int32_t *scratch = s.d_scratch + (size_t)g.first * max_task_polys() * 256;
         if (g.op == 0) {
             const int l = g.level == 2 ? 4 : g.level == 3 ? 5 : 7;
             dil::launch_sign_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->sk, ks->keys, s.d_msg,

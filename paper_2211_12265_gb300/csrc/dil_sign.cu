@@ -20,8 +20,9 @@ __global__ void __launch_bounds__(256, 4) k_sign(int n, const uint8_t *__restric
                            v.bar, v.lane);
     int it = 0;
     bool ok = false;
+    MaskStream ms{0, 0};
     while (it < max_iter) {
-        ok = sign_attempt<LEVEL, P>(it * V::L, scr, scr + Scratch<LEVEL>::PRE_POLYS * N, *v.gs, *v.ws, v.zt,
+        ok = sign_attempt<LEVEL, P>(it * V::L, scr, scr + Scratch<LEVEL>::PRE_POLYS * N, ms, *v.gs, *v.ws, v.zt,
                                     v.izt, v.g, v.bar, v.lane);
         ++it;
         if (ok) break;

@@ -178,7 +178,16 @@ def dil_sign_noalloc(level, n, sk, msg, msg_off, sig, task_status=None, stream=N
                                           _ptr(task_status), _stream(stream)), "dil_sign_noalloc")
 
 
-NOALLOC_MAX_TASKS = {2: 1489, 3: 963, 5: 606}
+def _sign_scratch_polys(level: int) -> int:
+    """Per-task scratch of the plain Sign kernel in polynomials: A^, s^1, s^2,
+    t^0, then the mask ring (l + 5), y^, w and z."""
+    k, l = {2: (4, 4), 3: (6, 5), 5: (8, 7)}[level]
+    return k * l + l + 2 * k + (l + 5) + l + k + l
+
+
+# Largest batch dil_sign_noalloc accepts: its 64 MiB static scratch over the
+# per-task scratch.
+NOALLOC_MAX_TASKS = {lv: (64 << 20) // (_sign_scratch_polys(lv) * 1024) for lv in (2, 3, 5)}
 
 
 def dil_keygen_host(ctx, level, n, seeds, pk, sk, stream=None):
