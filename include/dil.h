@@ -280,6 +280,14 @@ int dil_test_bounded_wait(dil_ctx *ctx, int flag_value, int limit, int *result);
  * (high, signed), 4 = warp shuffle.  Used for the integer roofline. */
 int dil_test_issue_rate(dil_ctx *ctx, int op, double *thread_ops_per_sm_clk);
 
+/* Test only: throughput of the Keccak-f[1600] forms the kernels use (section
+ * 3.3 of arXiv 2211.12265 describes the first), in SM clocks per state per
+ * round, 32 warps per SM, every state independent.  form: 1 = one state on 25
+ * lanes, 2 = two interleaved states, 6 = six states in the skewed row layout.
+ * Synchronous; allocates and frees a small buffer.  DIL_EINVAL for another
+ * form or a NULL output. */
+int dil_test_keccak_rate(dil_ctx *ctx, int form, double *sm_clocks_per_state_round);
+
 #ifdef __cplusplus
 }
 #endif

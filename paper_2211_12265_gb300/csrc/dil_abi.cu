@@ -647,4 +647,10 @@ int dil_test_issue_rate(dil_ctx *c, int op, double *thread_ops_per_sm_clk) {
     return status_of(dil::measure_issue_rate(op, thread_ops_per_sm_clk));
 }
 
+int dil_test_keccak_rate(dil_ctx *c, int form, double *sm_clocks_per_state_round) {
+    TEST_PROLOGUE(c)
+    if ((form != 1 && form != 2 && form != 6) || !sm_clocks_per_state_round) return DIL_EINVAL;
+    return status_of(dil::measure_keccak_rate(form, sm_clocks_per_state_round));
+}
+
 }  // extern "C"

@@ -1,11 +1,14 @@
-// Test-only probe behind dil_test_issue_rate: sustained issue rate of one
+// Test-only probes.  dil_test_issue_rate: sustained issue rate of one
 // integer instruction class, in thread-operations per SM clock, measured with
-// clock64() over independent dependency chains at full occupancy.  It gives
-// the denominator of the integer roofline the benchmark reports.
+// clock64() over independent dependency chains at full occupancy (the
+// denominator of the integer roofline the benchmark reports).
+// dil_test_keccak_rate: SM clocks per state per round of the three
+// Keccak-f[1600] forms the kernels use, 32 warps per SM.
 #include <cuda_runtime.h>
 
 #include <vector>
 
+#include "dil_keccak6.cuh"
 #include "dil_launch.h"
 
 namespace dil {
@@ -76,6 +79,69 @@ cudaError_t measure_issue_rate(int op, double *rate) {
     for (long long v : h) mean += (double)v;
     mean /= blocks;
     *rate = 2.0 * threads * PROBE_ITERS * 8 / mean;
+    return cudaSuccess;
+}
+
+constexpr int KPROBE_PERMS = 64;
+constexpr int KPROBE_WARPS = 8;
+constexpr int KPROBE_CTAS_PER_SM = 4;
+
+// Every warp permutes its FORM states (1: 25-lane form, 2: two interleaved
+// states, 6: six-state row form) KPROBE_PERMS times.
+template <int FORM>
+__global__ void __launch_bounds__(KPROBE_WARPS * 32, KPROBE_CTAS_PER_SM) k_keccak_probe(uint32_t *out,
+                                                                                       long long *cyc) {
+    __shared__ __align__(16) uint32_t sm[KPROBE_WARPS][640];   // 300 state words + 320 exchange words
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *kst = sm[warp], *kpi = kst + K6_STATES * K6_WORDS;
+    uint32_t lo = lane * 0x9E3779B9u + blockIdx.x, hi = lo ^ 0x5BD1E995u, lo1 = lo + 1, hi1 = hi + 1;
+    if (FORM == 6) {
+        for (int w = lane; w < K6_STATES * K6_WORDS; w += 32) kst[w] = w * 2654435761u + blockIdx.x;
+    }
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int i = 0; i < KPROBE_PERMS; ++i) {
+        if (FORM == 1) keccak_f(lo, hi);
+        if (FORM == 2) keccak_f2(lo, hi, lo1, hi1);
+        if (FORM == 6) keccak6_permute(kst, kpi);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = lo ^ hi ^ lo1 ^ hi1 ^ (FORM == 6 ? kst[lane] : 0u);
+}
+
+cudaError_t measure_keccak_rate(int form, double *clk_per_state_round) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = KPROBE_CTAS_PER_SM * sms, threads = KPROBE_WARPS * 32;
+    uint32_t *out = nullptr;
+    long long *cyc = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 4);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&cyc, (size_t)blocks * 8);
+    if (e != cudaSuccess) {
+        cudaFree(out);
+        return e;
+    }
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        if (form == 1) k_keccak_probe<1><<<blocks, threads>>>(out, cyc);
+        if (form == 2) k_keccak_probe<2><<<blocks, threads>>>(out, cyc);
+        if (form == 6) k_keccak_probe<6><<<blocks, threads>>>(out, cyc);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    std::vector<long long> h(blocks);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return e;
+    double mean = 0;
+    for (long long v : h) mean += (double)v;
+    mean /= blocks;
+    // one SM runs KPROBE_CTAS_PER_SM CTAs at once; its clock covers all their state-rounds
+    *clk_per_state_round = mean / ((double)KPROBE_CTAS_PER_SM * KPROBE_WARPS * form * KPROBE_PERMS * 24);
     return cudaSuccess;
 }
 

@@ -115,5 +115,6 @@ cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host);
 
 // test-only issue-rate probe (thread-ops per SM clock)
 cudaError_t measure_issue_rate(int op, double *rate);
+cudaError_t measure_keccak_rate(int form, double *clk_per_state_round);
 
 }  // namespace dil

@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_sample_in_ball": [P, I, S, P, P, P],
                 "dil_test_rounding": [P, I, S, P, P, P, P, P],
                 "dil_test_issue_rate": [P, I, P],
+                "dil_test_keccak_rate": [P, I, P],
                 "dil_test_bounded_wait": [P, I, I, P],
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
@@ -243,6 +244,13 @@ def dil_test_issue_rate(ctx, op: int) -> float:
     """Thread-ops per SM clock of one integer instruction class (see dil.h)."""
     r = ctypes.c_double()
     _check(load().dil_test_issue_rate(ctx, op, ctypes.byref(r)), "dil_test_issue_rate")
+    return r.value
+
+
+def dil_test_keccak_rate(ctx, form: int) -> float:
+    """SM clocks per state per round of a Keccak-f form (1, 2 or 6; see dil.h)."""
+    r = ctypes.c_double()
+    _check(load().dil_test_keccak_rate(ctx, form, ctypes.byref(r)), "dil_test_keccak_rate")
     return r.value
 
 

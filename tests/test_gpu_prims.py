@@ -113,3 +113,18 @@ def test_rounding_exhaustive(ctx, orc, level):
     assert np.array_equal(o[:, 2], d1) and np.array_equal(o[:, 3], d0)
     assert np.array_equal(o[:, 4], orc.make_hint(level, z, r))
     assert np.array_equal(o[:, 5], orc.use_hint(level, h, r))
+
+
+def test_probes_report_plausible_rates(ctx):
+    """The roofline probes: issue rates within the SM's 128 lanes per clock,
+    and the six-state Keccak form cheaper per state-round than the one-state
+    form it replaces in the samplers."""
+    from paper_2211_12265_gb300 import dil
+    for op in dil.ISSUE_OPS.values():
+        r = dil.dil_test_issue_rate(ctx.handle, op)
+        assert 1.0 < r <= 128.0, (op, r)
+    one = dil.dil_test_keccak_rate(ctx.handle, 1)
+    six = dil.dil_test_keccak_rate(ctx.handle, 6)
+    assert 0.5 < six < one, (six, one)
+    with pytest.raises(dil.DilError):
+        dil.dil_test_keccak_rate(ctx.handle, 3)
