@@ -54,6 +54,8 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 512 << 20
 
+STATIC_BATCH, STATIC_WAIT_S = 4096, 0.05   # static batching of the served comparison
+
 WORKLOADS = {
     "level2": dict(level=2, n=10000, config=2),
     "level3": dict(level=3, n=10000, config=3),
@@ -388,9 +390,15 @@ def served_summary(dev: int, n: int = 60000) -> dict:
             r = serving.summarize(rq, srv.replay(rq))
             r["offered_fraction"] = f
             rows.append(r)
+        # the same arrivals served by static batches (the plain one-launch-per-batch service)
+        srv.set_batching(STATIC_BATCH, STATIC_WAIT_S)
+        rq = serving.serving_workload(keys, n, rate=0.5 * sat["ops_s"], seed=102)
+        static = serving.summarize(rq, srv.replay(rq))
+        static["offered_fraction"] = 0.5
     return {"saturated_ops_s": sat["ops_s"], "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB log-uniform, "
                                                      "4096 resident keys per level, Poisson arrivals",
-            "streams": 4, "at_load": rows}
+            "streams": 4, "at_load": rows,
+            "static_batching": {"min_batch": STATIC_BATCH, "max_wait_s": STATIC_WAIT_S, "at_load": [static]}}
 
 
 def run_mixed(args, ranks: Ranks) -> dict:
@@ -466,9 +474,12 @@ def run_serving(args, ranks: Ranks) -> dict | None:
         srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=200))
         req = serving.serving_workload(keys, n, rate=1e9, seed=201)
         sat = serving.summarize(req, srv.replay(req))
-        rows = serving.sweep(srv, keys, [f * sat["ops_s"] for f in (0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.2)],
-                             n_per_rate=n, seed=210)
-        batches, carried = srv.stats()
+        fracs = (0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.2)
+        rows = serving.sweep(srv, keys, [f * sat["ops_s"] for f in fracs], n_per_rate=n, seed=210)
+        batches, carried, launches = srv.stats()
+        # the same arrival traces served by static batches (the plain one-launch-per-batch service)
+        srv.set_batching(STATIC_BATCH, STATIC_WAIT_S)
+        static = serving.sweep(srv, keys, [f * sat["ops_s"] for f in (0.1, 0.5, 0.9)], n_per_rate=n, seed=210)
     best = max(rows + [sat], key=lambda r: r["ops_s"])
     return {"metric": METRIC, "value": ranks.world * best["ops_s"], "unit": "ops/s", "n_gpus": ranks.world,
             "steps": len(rows) + 1, "warmup": 1, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True,
@@ -476,8 +487,11 @@ def run_serving(args, ranks: Ranks) -> dict | None:
             "config": {"workload": "served-mix", "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB "
                                                         "log-uniform, 4096 resident keys per level",
                        "requests_per_point": n, "streams": 4, "parallelism": f"replicas x{ranks.world}"},
-            "served": {"saturated": sat, "sweep": rows, "batches": batches, "requests": carried},
-            "gpu_launches": None}
+            "served": {"saturated": sat, "sweep": rows, "batches": batches, "requests": carried,
+                       "static_batching": {"min_batch": STATIC_BATCH, "max_wait_s": STATIC_WAIT_S,
+                                           "sweep": static}},
+            "gpu_launches": launches,
+            "gpu_launches_note": "keyed kernel launches of the warm-up, the saturated point and the continuous sweep"}
 
 
 def load_traffic(level: int, n: int):

@@ -209,6 +209,20 @@ int dil_server_create(int device, size_t memory_budget, int streams, int max_bat
 int dil_server_destroy(dil_server *srv);
 /* The admission limits chosen at creation. */
 int dil_server_limits(const dil_server *srv, int *max_batch, size_t *msg_capacity);
+/* Batching policy.  By default (max_wait_s = 0) a free slot takes whatever is
+ * pending (continuous batching).  With max_wait_s > 0 a slot starts only when
+ * at least min_batch requests are pending (capped by the admission limit) or
+ * the oldest pending request has waited max_wait_s seconds: static batching,
+ * the plain one-launch-per-batch service, kept for comparison.  DIL_EINVAL for
+ * min_batch < 1 or a negative wait. */
+int dil_server_set_batching(dil_server *srv, int min_batch, double max_wait_s);
+
+/* Launch shape of the server's keyed kernels for one operation (0 = Sign,
+ * 1 = Verify) and level: warps per CTA (1..8) and warps per task (1, 2, 4,
+ * dividing the former).  Defaults: Sign 8 and 4, Verify 4 and 1.  Takes
+ * effect for batches started afterwards.  DIL_EINVAL for other values. */
+int dil_server_set_tuning(dil_server *srv, int op, int level, int warps_per_cta, int warps_per_task);
+
 /* Installs n resident key pairs of one level (key ids 0..n-1), replacing the
  * level's previous store; only while no request is outstanding.  Synchronous. */
 int dil_server_add_keys(dil_server *srv, int level, size_t n, const uint8_t *pk, const uint8_t *sk);
@@ -226,8 +240,10 @@ int dil_server_poll(dil_server *srv, dil_result *out, size_t max_n, size_t *n_ou
 int dil_server_replay(dil_server *srv, size_t n, const double *arrival_s, const int32_t *op, const int32_t *level,
                       const int32_t *key, const uint8_t *msg, const uint64_t *msg_off, const uint8_t *sig_in,
                       uint8_t *sig_out, int32_t *status, uint8_t *ok, double *latency_s, double *wall_s);
-/* Batches dispatched and requests they carried since creation. */
-int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests);
+/* Batches dispatched, requests they carried and keyed-kernel launches (one
+ * per (operation, level) group of a batch) since creation.  Any output
+ * pointer may be NULL. */
+int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests, uint64_t *launches);
 
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
  * msg_off too).  They copy inputs to the device, run on `stream`, copy the

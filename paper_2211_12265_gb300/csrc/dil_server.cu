@@ -6,10 +6,17 @@
 // admission limits allow (max_batch requests, msg_capacity message bytes; the
 // slot's device buffers are sized once from the memory budget), groups them by
 // (operation, level), copies their inputs through pinned buffers, launches
-// the keyed kernels on the slot's stream and copies the results back.  New
-// requests therefore join as soon as any slot frees up, and batches on
-// different slots run concurrently on the device.  A request's latency runs
-// from its arrival to the moment its result is visible to the host.
+// the keyed kernels and copies the results back.  The groups of one batch run
+// concurrently on the slot's group streams (forked from and joined into the
+// slot's copy stream with events), so a batch takes as long as its slowest
+// group rather than the sum.  New requests therefore join as soon as any slot
+// frees up, and batches on different slots run concurrently on the device.
+// A request's latency runs from its arrival to the moment its result is
+// visible to the host.
+//
+// For comparison the dispatcher can also batch statically: a slot then starts
+// only when min_batch requests are pending or the oldest has waited
+// max_wait (the plain one-launch-per-batch service).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,9 +73,12 @@ struct Group {
     size_t sig_first;   // byte offset of the group's signatures
 };
 
+constexpr int MAX_GROUPS = 6;   // (operation, level) pairs
+
 struct Slot {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaStream_t stream = nullptr;          // copies in and out
+    cudaStream_t gstream[MAX_GROUPS] = {};  // one per group of a batch
+    cudaEvent_t done = nullptr, ev_in = nullptr, ev_grp[MAX_GROUPS] = {};
     bool busy = false;
     uint8_t *d_msg = nullptr, *d_sig_in = nullptr, *d_sig_out = nullptr, *d_ok = nullptr;
     uint64_t *d_off = nullptr;
@@ -99,7 +109,13 @@ struct dil_server {
     std::thread worker;
     bool stop = false;
     uint64_t next_id = 1;
-    uint64_t batches = 0, batched_reqs = 0;
+    uint64_t batches = 0, batched_reqs = 0, launches = 0;
+    int min_batch = 1;        // static batching: start a slot only with this many pending
+    double max_wait_s = 0;    // ... or once the oldest pending request waited this long
+    // launch shape per (operation, level): Sign 8 warps per CTA, 4 per task
+    // (short per-task latency); Verify 4 warps per CTA, one per task
+    int warps[2][3] = {{8, 8, 8}, {4, 4, 4}};
+    int wpt[2][3] = {{4, 4, 4}, {1, 1, 1}};
 };
 
 namespace {
@@ -110,6 +126,11 @@ void free_slot(Slot &s) {
     cudaFreeHost(s.h_msg); cudaFreeHost(s.h_sig_in); cudaFreeHost(s.h_sig_out); cudaFreeHost(s.h_ok);
     cudaFreeHost(s.h_off); cudaFreeHost(s.h_key); cudaFreeHost(s.h_status);
     if (s.done) cudaEventDestroy(s.done);
+    if (s.ev_in) cudaEventDestroy(s.ev_in);
+    for (int g = 0; g < MAX_GROUPS; ++g) {
+        if (s.ev_grp[g]) cudaEventDestroy(s.ev_grp[g]);
+        if (s.gstream[g]) cudaStreamDestroy(s.gstream[g]);
+    }
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
 }
@@ -118,6 +139,7 @@ bool alloc_slot(Slot &s, int max_batch, size_t msg_cap) {
     const size_t n = (size_t)max_batch, offs = n + 6;
     bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&s.d_msg, msg_cap + 16) == cudaSuccess &&
               cudaMalloc(&s.d_sig_in, n * MAX_SIG) == cudaSuccess &&
               cudaMalloc(&s.d_sig_out, n * MAX_SIG) == cudaSuccess && cudaMalloc(&s.d_ok, n) == cudaSuccess &&
@@ -129,6 +151,9 @@ bool alloc_slot(Slot &s, int max_batch, size_t msg_cap) {
               cudaMallocHost(&s.h_sig_out, n * MAX_SIG) == cudaSuccess && cudaMallocHost(&s.h_ok, n) == cudaSuccess &&
               cudaMallocHost(&s.h_off, offs * 8) == cudaSuccess && cudaMallocHost(&s.h_key, n * 4) == cudaSuccess &&
               cudaMallocHost(&s.h_status, n * 4) == cudaSuccess;
+    for (int g = 0; ok && g < MAX_GROUPS; ++g)
+        ok = cudaStreamCreateWithFlags(&s.gstream[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s.ev_grp[g], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) cudaGetLastError();
     return ok;
 }
@@ -147,8 +172,15 @@ void finish_request(dil_server *sv, Req *r, double t) {
 bool dispatch(dil_server *sv, Slot &s) {
     s.reqs.clear();
     s.groups.clear();
+    int warps[2][3], wpt[2][3];
     {
         std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->pending.empty()) return false;
+        if ((int)sv->pending.size() < std::min(sv->min_batch, sv->max_batch) &&
+            now_s() - sv->pending.front()->t_arrive < sv->max_wait_s && !sv->stop)
+            return false;   // static batching: wait for a fuller batch
+        memcpy(warps, sv->warps, sizeof(warps));
+        memcpy(wpt, sv->wpt, sizeof(wpt));
         size_t bytes = 0;
         while (!sv->pending.empty() && (int)s.reqs.size() < sv->max_batch) {
             Req *r = sv->pending.front();
@@ -192,20 +224,26 @@ bool dispatch(dil_server *sv, Slot &s) {
     bool any_verify = false;
     for (auto &g : s.groups) any_verify |= g.op == 1;
     if (any_verify) cudaMemcpyAsync(s.d_sig_in, s.h_sig_in, sig_off, cudaMemcpyHostToDevice, st);
-    for (auto &g : s.groups) {
+    cudaEventRecord(s.ev_in, st);
+    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
+        const Group &g = s.groups[gi];
         const int li = level_slot(g.level);
         dil_keystore *ks = sv->ks[li];
         int32_t *scratch = s.d_scratch + (size_t)g.first * max_task_polys() * 256;
+        cudaStream_t gs = s.gstream[gi];
+        cudaStreamWaitEvent(gs, s.ev_in, 0);
         if (g.op == 0) {
             const int l = g.level == 2 ? 4 : g.level == 3 ? 5 : 7;
             dil::launch_sign_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->sk, ks->keys, s.d_msg,
                                    s.d_off + g.off_first, s.d_sig_out + g.sig_first, s.d_status + g.first, nullptr,
-                                   scratch, (65536 - l) / l + 1, 8, 2, st);
+                                   scratch, (65536 - l) / l + 1, warps[0][li], wpt[0][li], gs);
         } else {
             dil::launch_verify_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->pk, ks->keys, ks->tr,
                                      s.d_msg, s.d_off + g.off_first, s.d_sig_in + g.sig_first, s.d_ok + g.first,
-                                     scratch, 8, 2, st);
+                                     scratch, warps[1][li], wpt[1][li], gs);
         }
+        cudaEventRecord(s.ev_grp[gi], gs);
+        cudaStreamWaitEvent(st, s.ev_grp[gi], 0);
     }
     cudaMemcpyAsync(s.h_sig_out, s.d_sig_out, sig_off, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(s.h_status, s.d_status, n * 4, cudaMemcpyDeviceToHost, st);
@@ -213,6 +251,7 @@ bool dispatch(dil_server *sv, Slot &s) {
     cudaEventRecord(s.done, st);
     s.busy = true;
     sv->batches++;
+    sv->launches += s.groups.size();
     sv->batched_reqs += n;
     return true;
 }
@@ -269,7 +308,7 @@ void worker_loop(dil_server *sv) {
         std::unique_lock<std::mutex> lk(sv->mu);
         if (sv->stop && !any_busy && sv->pending.empty()) return;
         if (!progressed) {
-            if (any_busy) {
+            if (any_busy || !sv->pending.empty()) {   // kernels running, or a static batch filling up
                 lk.unlock();
                 std::this_thread::sleep_for(std::chrono::microseconds(10));
             } else {
@@ -354,6 +393,25 @@ int dil_server_limits(const dil_server *sv, int *max_batch, size_t *msg_capacity
     if (!sv) return DIL_EINVAL;
     if (max_batch) *max_batch = sv->max_batch;
     if (msg_capacity) *msg_capacity = sv->msg_cap;
+    return DIL_OK;
+}
+
+int dil_server_set_batching(dil_server *sv, int min_batch, double max_wait_s) {
+    if (!sv || min_batch < 1 || !(max_wait_s >= 0)) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->min_batch = min_batch;
+    sv->max_wait_s = max_wait_s;
+    return DIL_OK;
+}
+
+int dil_server_set_tuning(dil_server *sv, int op, int level, int warps_per_cta, int warps_per_task) {
+    const int li = level_slot(level);
+    if (!sv || (op != 0 && op != 1) || li < 0 || warps_per_cta < 1 || warps_per_cta > 8) return DIL_EINVAL;
+    if (warps_per_task != 1 && warps_per_task != 2 && warps_per_task != 4) return DIL_EINVAL;
+    if (warps_per_cta % warps_per_task) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->warps[op][li] = warps_per_cta;
+    sv->wpt[op][li] = warps_per_task;
     return DIL_OK;
 }
 
@@ -487,10 +545,11 @@ int dil_server_replay(dil_server *sv, size_t n, const double *arrival_s, const i
     return DIL_OK;
 }
 
-int dil_server_stats(const dil_server *sv, uint64_t *batches, uint64_t *requests) {
+int dil_server_stats(const dil_server *sv, uint64_t *batches, uint64_t *requests, uint64_t *launches) {
     if (!sv) return DIL_EINVAL;
     if (batches) *batches = sv->batches;
     if (requests) *requests = sv->batched_reqs;
+    if (launches) *launches = sv->launches;
     return DIL_OK;
 }
 

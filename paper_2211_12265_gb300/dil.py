@@ -80,11 +80,13 @@ def load() -> ctypes.CDLL:
                 "dil_server_create": [I, S, I, I, P],
                 "dil_server_destroy": [P],
                 "dil_server_limits": [P, P, P],
+                "dil_server_set_batching": [P, I, ctypes.c_double],
+                "dil_server_set_tuning": [P, I, I, I, I],
                 "dil_server_add_keys": [P, I, S, P, P],
                 "dil_server_submit": [P, I, I, ctypes.c_int32, P, S, P, P],
                 "dil_server_poll": [P, P, S, P, I],
                 "dil_server_replay": [P, S, P, P, P, P, P, P, P, P, P, P, P, P],
-                "dil_server_stats": [P, P, P],
+                "dil_server_stats": [P, P, P, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -332,6 +334,14 @@ def dil_server_limits(srv) -> tuple[int, int]:
     return mb.value, mc.value
 
 
+def dil_server_set_batching(srv, min_batch: int, max_wait_s: float) -> None:
+    _check(load().dil_server_set_batching(srv, min_batch, max_wait_s), "dil_server_set_batching")
+
+
+def dil_server_set_tuning(srv, op: int, level: int, warps_per_cta: int, warps_per_task: int) -> None:
+    _check(load().dil_server_set_tuning(srv, op, level, warps_per_cta, warps_per_task), "dil_server_set_tuning")
+
+
 def dil_server_add_keys(srv, level, n, pk, sk) -> None:
     _check(load().dil_server_add_keys(srv, level, n, _ptr(pk), _ptr(sk)), "dil_server_add_keys")
 
@@ -359,10 +369,11 @@ def dil_server_replay(srv, n, arrival_s, op, level, key, msg, msg_off, sig_in, s
     return wall.value
 
 
-def dil_server_stats(srv) -> tuple[int, int]:
-    b, r = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(load().dil_server_stats(srv, ctypes.byref(b), ctypes.byref(r)), "dil_server_stats")
-    return b.value, r.value
+def dil_server_stats(srv) -> tuple[int, int, int]:
+    """(batches, requests, kernel launches) since the server was created."""
+    b, r, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().dil_server_stats(srv, ctypes.byref(b), ctypes.byref(r), ctypes.byref(k)), "dil_server_stats")
+    return b.value, r.value, k.value
 
 
 # ----------------------------------------------------------------- wrapper

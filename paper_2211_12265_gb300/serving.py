@@ -33,6 +33,14 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
+    def set_batching(self, min_batch: int = 1, max_wait_s: float = 0.0) -> None:
+        """Continuous batching by default; min_batch / max_wait_s > 0 make the
+        dispatcher batch statically (see dil_server_set_batching)."""
+        dil.dil_server_set_batching(self.handle, min_batch, max_wait_s)
+
+    def set_tuning(self, op: int, level: int, warps_per_cta: int, warps_per_task: int) -> None:
+        dil.dil_server_set_tuning(self.handle, op, level, warps_per_cta, warps_per_task)
+
     def add_keys(self, level: int, pk: np.ndarray, sk: np.ndarray) -> None:
         pk = np.ascontiguousarray(pk, dtype=np.uint8)
         sk = np.ascontiguousarray(sk, dtype=np.uint8)
@@ -55,7 +63,8 @@ class Server:
                                      req["msg"], req["msg_off"], req["sig_in"], sig_out, status, ok, lat)
         return {"sig": sig_out, "status": status, "ok": ok, "latency": lat, "wall": wall}
 
-    def stats(self) -> tuple[int, int]:
+    def stats(self) -> tuple[int, int, int]:
+        """(batches, requests, kernel launches) since creation."""
         return dil.dil_server_stats(self.handle)
 
 

@@ -68,7 +68,7 @@ def test_server_alone_and_in_the_mix(keys):
         for lv in keys:
             srv.add_keys(lv, *keys[lv])
         mix = srv.replay(req)
-        batches, carried = srv.stats()
+        batches, carried, launches = srv.stats()
         assert carried == n and batches >= 3       # several batches, some in flight together
         alone_sig = np.zeros_like(mix["sig"])
         alone_ok = np.zeros_like(mix["ok"])
@@ -104,3 +104,30 @@ def test_server_admission_small_budget(keys):
         req = serving.serving_workload(keys, 150, rate=1e6, seed=5, hi=3000)
         out = srv.replay(req)
     assert out["ok"][req["op"] == 1].all() and (out["status"][req["op"] == 0] == 0).all()
+
+
+def test_server_policies_and_shapes_agree(keys):
+    """Static batching, continuous batching and other launch shapes of the
+    keyed kernels give byte-identical results on the same arrival trace."""
+    from paper_2211_12265_gb300 import dil, serving
+    req = serving.serving_workload(keys, 200, rate=5e5, seed=9, hi=4000)
+    with serving.Server(0, memory_budget=512 << 20, streams=2, max_batch=128) as srv:
+        for lv in keys:
+            srv.add_keys(lv, *keys[lv])
+        base = srv.replay(req)
+        srv.set_batching(64, 0.002)
+        static = srv.replay(req)
+        srv.set_batching(1, 0.0)
+        for lv in keys:
+            srv.set_tuning(0, lv, 2, 1)
+            srv.set_tuning(1, lv, 8, 2)
+        shaped = srv.replay(req)
+        with pytest.raises(dil.DilError):
+            srv.set_tuning(0, 2, 6, 4)             # 4 does not divide 6
+        with pytest.raises(dil.DilError):
+            srv.set_batching(0, 0.0)
+    sign = req["op"] == 0
+    for other in (static, shaped):
+        assert np.array_equal(base["sig"][sign], other["sig"][sign])
+        assert np.array_equal(base["status"], other["status"]) and (base["status"][sign] == 0).all()
+        assert np.array_equal(base["ok"][~sign], other["ok"][~sign]) and base["ok"][~sign].all()
