@@ -246,8 +246,12 @@ int dil_server_replay(dil_server *srv, size_t n, const double *arrival_s, const 
 int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests, uint64_t *launches);
 
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
- * msg_off too).  They copy inputs to the device, run on `stream`, copy the
- * results back and synchronise the stream before returning. */
+ * msg_off too; pinned memory lets the copies overlap).  They copy inputs to
+ * the device, run, copy the results back and synchronise `stream` before
+ * returning.  A batch of 2048 tasks or more is cut into four chunks, each on
+ * its own stream (`stream` and three of the context's), so one chunk's copies
+ * overlap the others' kernels (section 4.4 multi-stream overlap); the staging
+ * buffers grow on demand and are not part of the workspace budget. */
 int dil_keygen_host(dil_ctx *ctx, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
                     void *stream);
 int dil_sign_host(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,

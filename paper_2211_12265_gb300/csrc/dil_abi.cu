@@ -32,6 +32,9 @@ struct dil_ctx {
     dil::PersistTuning gtune;
     int gmax_iter = -1;
     void *gws = nullptr;
+    // host-form pipeline: extra streams and the fork / join events
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::mutex mu;
 };
 
@@ -143,6 +146,10 @@ int dil_ctx_destroy(dil_ctx *c) {
         if (c->pws) cudaFree(c->pws);
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        for (cudaStream_t a : c->aux)
+            if (a) cudaStreamDestroy(a);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
     }
     delete c;
     return DIL_OK;
@@ -459,6 +466,8 @@ int dil_verify_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t
     return DIL_OK;
 }
 
+}  // extern "C"
+
 // ---------------------------------------------------------------- host forms
 namespace {
 
@@ -481,103 +490,175 @@ int ensure_stage(dil_ctx *c, size_t bytes) {
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Host-buffer forms as a pipeline (the paper's section 4.4 multi-stream
+// overlap): a large batch is cut into PIPE_STREAMS chunks, each on its own
+// stream (the caller's and the context's extra ones) with its own part of the
+// workspace.  A chunk copies its inputs in, runs its kernel and copies its
+// outputs back; the chunks' kernels run concurrently (together they fill the
+// GPU like one launch, and their tails overlap), while the copies of one
+// chunk overlap the kernels of the others.  When the budget cannot hold the
+// whole batch's scratch, chunks shrink and cycle over the streams.
+constexpr size_t PIPE_MIN_TASKS = 2048;   // smaller batches run as one chunk
+constexpr size_t PIPE_STREAMS = 4;
+
+int ensure_aux(dil_ctx *c) {
+    if (c->aux[0]) return DIL_OK;
+    for (cudaStream_t &a : c->aux)
+        if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return DIL_ECUDA;
+        }
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return DIL_ECUDA;
+    }
+    return DIL_OK;
+}
+
+// Runs chunk(c0, c1, stream, scratch) over the batch and waits for the
+// caller's stream.  `per_task` is the kernel scratch of one task.
+template <class Chunk>
+int run_pipeline(dil_ctx *c, size_t n, size_t per_task, cudaStream_t s0, Chunk chunk) {
+    const size_t ns = n >= PIPE_MIN_TASKS ? PIPE_STREAMS : 1;
+    size_t per = (n + ns - 1) / ns;
+    const size_t fit = per_task ? c->budget / (ns * per_task) : per;
+    if (fit == 0) return DIL_ENOMEM;
+    per = std::min(per, fit);
+    const size_t k = (n + per - 1) / per;
+    int rc = ensure_ws(c, ns * per * per_task);
+    if (!rc && ns > 1) rc = ensure_aux(c);
+    if (rc) return rc;
+    cudaStream_t st[PIPE_STREAMS] = {s0, c->aux[0], c->aux[1], c->aux[2]};
+    if (ns > 1) {
+        if (cudaEventRecord(c->ev_fork, s0) != cudaSuccess) return DIL_ECUDA;
+        for (size_t j = 1; j < ns; ++j)
+            if (cudaStreamWaitEvent(st[j], c->ev_fork, 0) != cudaSuccess) return DIL_ECUDA;
+    }
+    for (size_t i = 0; i < k && !rc; ++i) {
+        const size_t c0 = i * per, c1 = std::min(n, c0 + per);
+        int32_t *scratch = (int32_t *)c->ws + (i % ns) * per * (per_task / sizeof(int32_t));
+        rc = chunk(c0, c1, st[i % ns], scratch);
+    }
+    for (size_t j = 1; j < ns; ++j)
+        if ((cudaEventRecord(c->ev_join, st[j]) != cudaSuccess ||
+             cudaStreamWaitEvent(s0, c->ev_join, 0) != cudaSuccess) && !rc)
+            rc = DIL_ECUDA;
+    const cudaError_t e = cudaStreamSynchronize(s0);
+    if (rc) return rc;
+    return e == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
+bool h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+}
+bool d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+}
+
 }  // namespace
+
+extern "C" {
 
 int dil_keygen_host(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
                     void *stream) {
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
-    if (!seeds || !pk || !sk) return DIL_EINVAL;
+    if (!seeds || !pk || !sk || n > (size_t)INT32_MAX) return DIL_EINVAL;
     size_t pkb, skb, sigb;
     sizes_of(level, pkb, skb, sigb);
-    uint8_t *d_seed, *d_pk, *d_sk;
-    {
-        std::lock_guard<std::mutex> lk(c->mu);
-        DeviceGuard g(c->device);
-        int rc = ensure_stage(c, al(32 * n) + al(pkb * n) + al(skb * n));
-        if (rc) return rc;
-        d_seed = (uint8_t *)c->stage;
-        d_pk = d_seed + al(32 * n);
-        d_sk = d_pk + al(pkb * n);
-    }
+    std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d_seed, seeds, 32 * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    int rc = dil_keygen(c, level, n, d_seed, d_pk, d_sk, stream);
+    int rc = ensure_stage(c, al(32 * n) + al(pkb * n) + al(skb * n));
     if (rc) return rc;
-    if (cudaMemcpyAsync(pk, d_pk, pkb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
-    if (cudaMemcpyAsync(sk, d_sk, skb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+    uint8_t *d_seed = (uint8_t *)c->stage, *d_pk = d_seed + al(32 * n), *d_sk = d_pk + al(pkb * n);
+    const int w = c->warps[0][lidx(level)], p = c->wpt[0][lidx(level)];
+    return run_pipeline(c, n, dil::scratch_polys(dil::OP_KEYGEN, level) * POLY_BYTES, (cudaStream_t)stream,
+                        [&](size_t c0, size_t c1, cudaStream_t s, int32_t *scratch) -> int {
+                            const size_t m = c1 - c0;
+                            if (!h2d(d_seed + 32 * c0, seeds + 32 * c0, 32 * m, s)) return DIL_ECUDA;
+                            cudaError_t e = dil::launch_keygen(level, (int)m, d_seed + 32 * c0, d_pk + pkb * c0,
+                                                               d_sk + skb * c0, scratch, w, p, s);
+                            if (e != cudaSuccess) return cuda_fail(e);
+                            if (!d2h(pk + pkb * c0, d_pk + pkb * c0, pkb * m, s) ||
+                                !d2h(sk + skb * c0, d_sk + skb * c0, skb * m, s))
+                                return DIL_ECUDA;
+                            return DIL_OK;
+                        });
 }
 
 int dil_sign_host(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
                   uint8_t *sig, int32_t *task_status, void *stream) {
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
-    if (!sk || !msg_off || !sig) return DIL_EINVAL;
+    if (!sk || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
     size_t pkb, skb, sigb;
     sizes_of(level, pkb, skb, sigb);
-    size_t mlen = (size_t)msg_off[n];
+    const size_t mlen = (size_t)msg_off[n];
     if (mlen && !msg) return DIL_EINVAL;
-    uint8_t *d_sk, *d_msg, *d_sig;
-    uint64_t *d_off;
-    int32_t *d_st;
-    {
-        std::lock_guard<std::mutex> lk(c->mu);
-        DeviceGuard g(c->device);
-        int rc = ensure_stage(c, al(skb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(4 * n));
-        if (rc) return rc;
-        d_sk = (uint8_t *)c->stage;
-        d_msg = d_sk + al(skb * n);
-        d_off = (uint64_t *)(d_msg + al(mlen + 1));
-        d_sig = (uint8_t *)d_off + al(8 * (n + 1));
-        d_st = (int32_t *)(d_sig + al(sigb * n));
-    }
+    std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d_sk, sk, skb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    if (mlen && cudaMemcpyAsync(d_msg, msg, mlen, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    if (cudaMemcpyAsync(d_off, msg_off, 8 * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    int rc = dil_sign(c, level, n, d_sk, d_msg, d_off, d_sig, d_st, stream);
+    int rc = ensure_stage(c, al(skb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(4 * n));
     if (rc) return rc;
-    if (cudaMemcpyAsync(sig, d_sig, sigb * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
-    if (task_status && cudaMemcpyAsync(task_status, d_st, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return DIL_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+    uint8_t *d_sk = (uint8_t *)c->stage, *d_msg = d_sk + al(skb * n);
+    uint64_t *d_off = (uint64_t *)(d_msg + al(mlen + 1));
+    uint8_t *d_sig = (uint8_t *)d_off + al(8 * (n + 1));
+    int32_t *d_st = (int32_t *)(d_sig + al(sigb * n));
+    const int l = level == 2 ? 4 : level == 3 ? 5 : 7, cap = (65536 - l) / l + 1;
+    const int max_iter = (c->max_iter > 0 && c->max_iter < cap) ? c->max_iter : cap;
+    const int w = c->warps[1][lidx(level)], p = c->wpt[1][lidx(level)];
+    return run_pipeline(c, n, dil::scratch_polys(dil::OP_SIGN, level) * POLY_BYTES, (cudaStream_t)stream,
+                        [&](size_t c0, size_t c1, cudaStream_t s, int32_t *scratch) -> int {
+                            const size_t m = c1 - c0;
+                            if (!h2d(d_sk + skb * c0, sk + skb * c0, skb * m, s) ||
+                                !h2d(d_msg + msg_off[c0], msg ? msg + msg_off[c0] : nullptr,
+                                     (size_t)(msg_off[c1] - msg_off[c0]), s) ||
+                                !h2d(d_off + c0, msg_off + c0, 8 * (m + 1), s))
+                                return DIL_ECUDA;
+                            cudaError_t e = dil::launch_sign(level, (int)m, d_sk + skb * c0, d_msg, d_off + c0,
+                                                             d_sig + sigb * c0, d_st + c0, nullptr, scratch,
+                                                             max_iter, w, p, s);
+                            if (e != cudaSuccess) return cuda_fail(e);
+                            if (!d2h(sig + sigb * c0, d_sig + sigb * c0, sigb * m, s) ||
+                                (task_status && !d2h(task_status + c0, d_st + c0, 4 * m, s)))
+                                return DIL_ECUDA;
+                            return DIL_OK;
+                        });
 }
 
 int dil_verify_host(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
                     const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream) {
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
-    if (!pk || !msg_off || !sig || !ok) return DIL_EINVAL;
+    if (!pk || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;
     size_t pkb, skb, sigb;
     sizes_of(level, pkb, skb, sigb);
-    size_t mlen = (size_t)msg_off[n];
+    const size_t mlen = (size_t)msg_off[n];
     if (mlen && !msg) return DIL_EINVAL;
-    uint8_t *d_pk, *d_msg, *d_sig, *d_ok;
-    uint64_t *d_off;
-    {
-        std::lock_guard<std::mutex> lk(c->mu);
-        DeviceGuard g(c->device);
-        int rc = ensure_stage(c, al(pkb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(n));
-        if (rc) return rc;
-        d_pk = (uint8_t *)c->stage;
-        d_msg = d_pk + al(pkb * n);
-        d_off = (uint64_t *)(d_msg + al(mlen + 1));
-        d_sig = (uint8_t *)d_off + al(8 * (n + 1));
-        d_ok = d_sig + al(sigb * n);
-    }
+    std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d_pk, pk, pkb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    if (mlen && cudaMemcpyAsync(d_msg, msg, mlen, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    if (cudaMemcpyAsync(d_off, msg_off, 8 * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    if (cudaMemcpyAsync(d_sig, sig, sigb * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return DIL_ECUDA;
-    int rc = dil_verify(c, level, n, d_pk, d_msg, d_off, d_sig, d_ok, stream);
+    int rc = ensure_stage(c, al(pkb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(n));
     if (rc) return rc;
-    if (cudaMemcpyAsync(ok, d_ok, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DIL_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+    uint8_t *d_pk = (uint8_t *)c->stage, *d_msg = d_pk + al(pkb * n);
+    uint64_t *d_off = (uint64_t *)(d_msg + al(mlen + 1));
+    uint8_t *d_sig = (uint8_t *)d_off + al(8 * (n + 1));
+    uint8_t *d_ok = d_sig + al(sigb * n);
+    const int w = c->warps[2][lidx(level)], p = c->wpt[2][lidx(level)];
+    return run_pipeline(c, n, dil::scratch_polys(dil::OP_VERIFY, level) * POLY_BYTES, (cudaStream_t)stream,
+                        [&](size_t c0, size_t c1, cudaStream_t s, int32_t *scratch) -> int {
+                            const size_t m = c1 - c0;
+                            if (!h2d(d_pk + pkb * c0, pk + pkb * c0, pkb * m, s) ||
+                                !h2d(d_msg + msg_off[c0], msg ? msg + msg_off[c0] : nullptr,
+                                     (size_t)(msg_off[c1] - msg_off[c0]), s) ||
+                                !h2d(d_off + c0, msg_off + c0, 8 * (m + 1), s) ||
+                                !h2d(d_sig + sigb * c0, sig + sigb * c0, sigb * m, s))
+                                return DIL_ECUDA;
+                            cudaError_t e = dil::launch_verify(level, (int)m, d_pk + pkb * c0, d_msg, d_off + c0,
+                                                               d_sig + sigb * c0, d_ok + c0, scratch, w, p, s);
+                            if (e != cudaSuccess) return cuda_fail(e);
+                            if (!d2h(ok + c0, d_ok + c0, m, s)) return DIL_ECUDA;
+                            return DIL_OK;
+                        });
 }
 
 // ---------------------------------------------------------------- test-only

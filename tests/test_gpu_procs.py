@@ -162,6 +162,41 @@ def test_host_forms_match_device_forms(ctx, orc):
     assert ok.all()
 
 
+def test_host_pipeline_chunks_match_device_forms(orc):
+    """A batch large enough for the chunked two-stream host pipeline (with a
+    budget that forces extra, smaller chunks) gives the device forms' bytes;
+    sampled tasks against the oracle."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    level, n = 2, 3001                              # 4 ragged chunks
+    seeds, msg, off = _batch(orc, level, n, 17, "uniform", 0, 200)
+    pkb, skb, sigb = dil.SIZES[level]
+    for budget in (0, 300 * dil._sign_scratch_polys(level) * 1024):
+        c = dil.Context(0, budget)
+        try:
+            pk = np.zeros((n, pkb), np.uint8)
+            sk = np.zeros((n, skb), np.uint8)
+            dil.dil_keygen_host(c.handle, level, n, seeds, pk, sk)
+            dpk, dsk = c.keygen(level, dev(seeds))
+            assert np.array_equal(pk, host(dpk)) and np.array_equal(sk, host(dsk))
+            sig = np.zeros((n, sigb), np.uint8)
+            st = np.zeros(n, np.int32)
+            dil.dil_sign_host(c.handle, level, n, sk, msg, off, sig, st)
+            dsig, dst = c.sign(level, dsk, dev(msg), dev(off))
+            assert np.array_equal(sig, host(dsig)) and (st == 0).all()
+            bad = sig.copy()
+            bad[::5, 7] ^= 4
+            ok = np.zeros(n, np.uint8)
+            dil.dil_verify_host(c.handle, level, n, pk, msg, off, bad, ok)
+            assert np.array_equal(ok.astype(bool), np.arange(n) % 5 != 0)
+        finally:
+            c.close()
+    for i in (0, 751, 1502, 3000):
+        _, s, _ = orc.sign(level, sk[i].tobytes(), msg[off[i]:off[i + 1]].tobytes())
+        assert s == sig[i].tobytes()
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (2, 2), (4, 2), (4, 4), (8, 4), (8, 1)])
 @pytest.mark.parametrize("level", [2, 3, 5])
 def test_launch_shapes_bit_exact(orc, level, shape):
