@@ -127,7 +127,7 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
         const int r = *(volatile int *)&gs.claim2;
         group_sync<P>(bar);
         if (r < 0) break;
-        if (sign_attempt<LEVEL, P>(Lv<LEVEL>::L * r, pre, itr, ms, gs, ws, zt, izt, g, bar, lane)) {
+        if (sign_attempt<LEVEL, P>(Lv<LEVEL>::L * r, pre, itr, ms, gs, ws, zt, izt, g, bar, lane, &tk.best_r, r)) {
             commit<LEVEL, P>(pc, tk, r, jb, local, itr, gs, g, bar, lane);
             break;
         }

@@ -504,9 +504,13 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
 // gs.ctilde, scratch Z and gs.hmask hold the signature parts.
 // pre: the task's precomputation part (possibly prepared by another warp
 // group, so it is read through L2); itr: this worker's per-repetition part.
+// stop_below / rep: a speculative repetition rep of the persistent form
+// stops before hashing c~ once *stop_below (the smallest accepting repetition
+// found so far) is below rep; it then reports a rejection.
 template <int LEVEL, int P>
 __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
-                             WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
+                             WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
+                             const int *stop_below = nullptr, int rep = 0) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     volatile int *vflag = &gs.flag;
@@ -545,15 +549,20 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskSt
     group_sync<P>(bar);
     // c~ = H(mu || w1)  (l.9)
     if (g == 0) {
-        uint32_t lo = 0, hi = 0;
-        absorb_smem(lo, hi, gs.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
-        squeeze_words(lo, hi, gs.ctilde, 4, lane);
+        int stop = 0;
+        if (stop_below) stop = __shfl_sync(FULL, lane == 0 ? (int)(__ldcg(stop_below) < rep) : 0, 0);
+        if (!stop) {
+            uint32_t lo = 0, hi = 0;
+            absorb_smem(lo, hi, gs.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);
+            squeeze_words(lo, hi, gs.ctilde, 4, lane);
+        }
         if (lane == 0) {
-            gs.flag = 0;
+            gs.flag = stop;
             gs.count = 0;
         }
     }
     group_sync<P>(bar);
+    if (*vflag) return false;
     // c^ = NTT(SampleInBall(c~))  (l.10)
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta  (l.11, l.14)
