@@ -39,7 +39,7 @@ struct KLane {
     int b0, b1, b2;    // pi+chi: sources of B[x,y], B[x+1,y], B[x+2,y]
     int rot;           // rho amount mod 32
     bool swap;         // rho amount >= 32
-    bool lane0;        // holds lane (0,0) (iota)
+    uint32_t iota;     // all ones on the thread holding lane (0,0), else 0
 };
 
 __device__ __forceinline__ KLane klane_init(int lane) {
@@ -59,7 +59,7 @@ __device__ __forceinline__ KLane klane_init(int lane) {
     int r = rho_offset(x, y);
     k.rot = r & 31;
     k.swap = r >= 32;
-    k.lane0 = lane == 0;
+    k.iota = lane == 0 ? 0xFFFFFFFFu : 0u;
     return k;
 }
 
@@ -90,17 +90,19 @@ __device__ __forceinline__ void keccak_round(uint32_t &lo, uint32_t &hi, const K
     lo = a0l ^ (~a1l & a2l);
     hi = a0h ^ (~a1h & a2h);
     // iota (branch-free, so that two interleaved rounds form one basic block)
-    lo ^= k.lane0 ? (uint32_t)rc : 0u;
-    hi ^= k.lane0 ? (uint32_t)(rc >> 32) : 0u;
+    lo ^= (uint32_t)rc & k.iota;
+    hi ^= (uint32_t)(rc >> 32) & k.iota;
 }
 
 // Out-of-line permutations, called by value so the state stays in registers.
 // The lane parameters are recomputed per call (a few dozen instructions per
-// 24 rounds) instead of occupying registers at every call site.
+// 24 rounds) instead of occupying registers at every call site.  The round
+// loops stay rolled: the fused kernels are bound by instruction fetch as much
+// as by issue, and unrolling them cost more than the saved loop overhead.
 static __device__ __noinline__ uint2 keccak_f_impl(uint2 s) {
     const KLane k = klane_init(threadIdx.x & 31);
     uint32_t lo = s.x, hi = s.y;
-#pragma unroll 2
+#pragma unroll 1
     for (int r = 0; r < 24; ++r) keccak_round(lo, hi, k, c_keccak_rc[r]);
     return make_uint2(lo, hi);
 }
@@ -110,7 +112,7 @@ static __device__ __noinline__ uint2 keccak_f_impl(uint2 s) {
 static __device__ __noinline__ uint4 keccak_f2_impl(uint4 s) {
     const KLane k = klane_init(threadIdx.x & 31);
     uint32_t lo0 = s.x, hi0 = s.y, lo1 = s.z, hi1 = s.w;
-#pragma unroll 2
+#pragma unroll 1
     for (int r = 0; r < 24; ++r) {
         const uint64_t rc = c_keccak_rc[r];
         keccak_round(lo0, hi0, k, rc);

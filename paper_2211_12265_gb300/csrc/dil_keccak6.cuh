@@ -99,7 +99,7 @@ static __device__ __noinline__ void keccak6_permute_impl(uint32_t kst, uint32_t 
                      : "r"(row + 8 * (w >> 27)));
     }
     const uint32_t rd = kpi + 4 * lane;
-    const bool has00 = on && y == 0;
+    const uint32_t iota_mask = (on && y == 0) ? 0xFFFFFFFFu : 0u;   // lane (0, 0) sits in slot 0 of row 0
 #pragma unroll 1
     for (int round = 0; round < 24; ++round) {
         // theta, reduce-scatter: lane y collects column y (slot 5 - k of row y + k)
@@ -152,8 +152,8 @@ static __device__ __noinline__ void keccak6_permute_impl(uint32_t kst, uint32_t 
         }
         // iota on lane (0, 0): slot 0 of row 0
         const uint64_t rc = c_keccak_rc[round];
-        a[0] ^= has00 ? (uint32_t)rc : 0u;
-        a[1] ^= has00 ? (uint32_t)(rc >> 32) : 0u;
+        a[0] ^= (uint32_t)rc & iota_mask;
+        a[1] ^= (uint32_t)(rc >> 32) & iota_mask;
     }
     if (on) {
 #pragma unroll
