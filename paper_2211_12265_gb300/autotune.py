@@ -44,8 +44,24 @@ def _timer(torch, flush):
     return timeit
 
 
-def tune(levels=(2, 3, 5), n: int = 10000, device: int = 0, log=print) -> dict:
-    """Measures every candidate shape; returns the table of the fastest."""
+def _persistent_sweep(dil, ctx, jobs, timeit, n_tasks, label, log) -> dict:
+    best = None
+    for shape in PERSIST_SHAPES:
+        dil.dil_set_persistent_tuning(ctx.handle, *shape)
+        t = timeit(lambda: dil.dil_sign_persistent(ctx.handle, jobs))
+        assert dil.dil_persistent_status(ctx.handle) == dil.OK
+        log(f"{label} sign   persistent {shape}: {n_tasks / t * 1e3:11.0f}/s")
+        if best is None or t < best[1]:
+            best = (shape, t)
+    s = best[0]
+    return {"warps_per_cta": s[0], "warps_per_task": s[1], "ctas_per_sm": s[2], "chunk": s[3], "speculation": s[4],
+            "ops_s": n_tasks / best[1] * 1e3}
+
+
+def tune(levels=(2, 3, 5), n: int = 10000, device: int = 0, log=print, mixed_n: int = 100000) -> dict:
+    """Measures every candidate shape; returns the table of the fastest.  The
+    persistent Sign is tuned per level on n tasks and, as "mixed", on one
+    launch of mixed_n Dilithium2 plus mixed_n Dilithium5 tasks."""
     import numpy as np
     import torch
 
@@ -79,19 +95,21 @@ def tune(levels=(2, 3, 5), n: int = 10000, device: int = 0, log=print) -> dict:
                 ctx.set_tuning(OPS[name], best[0][0], best[0][1], level)
                 table["plain"][str(level)][name] = {"warps_per_cta": best[0][0], "warps_per_task": best[0][1],
                                                     "ops_s": n / best[1] * 1e3}
-            # restore the level's signature / status before the persistent sweep
             job = [dil.sign_job(level, n, sk, msg, off, sig, st)]
-            best = None
-            for shape in PERSIST_SHAPES:
-                dil.dil_set_persistent_tuning(ctx.handle, *shape)
-                t = timeit(lambda: dil.dil_sign_persistent(ctx.handle, job))
-                assert dil.dil_persistent_status(ctx.handle) == dil.OK
-                log(f"level {level} sign   persistent {shape}: {n / t * 1e3:11.0f}/s")
-                if best is None or t < best[1]:
-                    best = (shape, t)
-            s = best[0]
-            table["persistent"][str(level)] = {"warps_per_cta": s[0], "warps_per_task": s[1], "ctas_per_sm": s[2],
-                                              "chunk": s[3], "speculation": s[4], "ops_s": n / best[1] * 1e3}
+            table["persistent"][str(level)] = _persistent_sweep(dil, ctx, job, timeit, n, f"level {level}", log)
+        if mixed_n and {2, 5} <= set(levels):
+            jobs, keep = [], []
+            for level in (2, 5):
+                w = W.workload(4, mixed_n)
+                seeds = torch.from_numpy(W.seeds(mixed_n, 4 + level)).cuda()
+                msg = torch.from_numpy(w["msg"]).cuda()
+                off = torch.from_numpy(w["msg_off"]).cuda()
+                pk, sk = ctx.keygen(level, seeds)
+                sig = torch.empty((mixed_n, dil.SIZES[level][2]), dtype=torch.uint8, device="cuda")
+                st = torch.empty(mixed_n, dtype=torch.int32, device="cuda")
+                keep.append((sk, msg, off, sig, st))
+                jobs.append(dil.sign_job(level, mixed_n, sk, msg, off, sig, st))
+            table["persistent"]["mixed"] = _persistent_sweep(dil, ctx, jobs, timeit, 2 * mixed_n, "levels 2+5", log)
     return table
 
 
@@ -110,10 +128,10 @@ def save(table: dict, path: str | None = None) -> str:
     return path
 
 
-def apply(ctx, table: dict | None = None, persistent_level: int | None = None) -> None:
+def apply(ctx, table: dict | None = None, persistent_level: int | str | None = None) -> None:
     """Installs the plain shapes of every level and the persistent shape of
-    `persistent_level` (default: the slowest level, whose tail dominates a
-    mixed launch) on a dil.Context."""
+    `persistent_level` (a level, or "mixed" for launches that mix levels;
+    default: "mixed" when tuned, else the slowest level) on a dil.Context."""
     from . import dil
     table = table or load()
     if not table:
@@ -123,7 +141,12 @@ def apply(ctx, table: dict | None = None, persistent_level: int | None = None) -
             ctx.set_tuning(OPS[name], v["warps_per_cta"], v["warps_per_task"], int(level))
     pers = table.get("persistent", {})
     if pers:
-        lv = str(persistent_level) if persistent_level and str(persistent_level) in pers else max(pers, key=int)
+        if persistent_level and str(persistent_level) in pers:
+            lv = str(persistent_level)
+        elif "mixed" in pers:
+            lv = "mixed"
+        else:
+            lv = max((k for k in pers if k.isdigit()), key=int)
         v = pers[lv]
         dil.dil_set_persistent_tuning(ctx.handle, v["warps_per_cta"], v["warps_per_task"], v["ctas_per_sm"],
                                       v["chunk"], v["speculation"])
