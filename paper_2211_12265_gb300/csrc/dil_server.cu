@@ -1,11 +1,13 @@
 // Serving loop: continuous batching of mixed Sign / Verify requests of any
 // level and message length over resident keys.
 //
-// A dispatcher thread owns S stream slots.  Whenever a slot is free and
-// requests are pending it takes them in arrival order, as many as the slot's
-// admission limits allow (max_batch requests, msg_capacity message bytes; the
-// slot's device buffers are sized once from the memory budget), groups them by
-// (operation, level), copies their inputs through pinned buffers, launches
+// Each of the S stream slots has its own dispatcher thread.  Whenever its slot
+// is free and requests are pending it takes them in arrival order, as many as
+// the slot's admission limits allow (max_batch requests, msg_capacity message
+// bytes; the slot's device buffers are sized once from the memory budget) and,
+// under a backlog, about a 1/S share of it, so that the slots split a burst
+// instead of one slot taking it all.  It groups them by (operation, level),
+// copies their inputs through pinned buffers, launches
 // the keyed kernels and copies the results back.  The groups of one batch run
 // concurrently on the slot's group streams (forked from and joined into the
 // slot's copy stream with events), so a batch takes as long as its slowest
@@ -20,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -106,10 +109,10 @@ struct dil_server {
     std::deque<Req *> pending;
     std::deque<Req *> completed;
     size_t outstanding = 0;   // submitted and not yet completed
-    std::thread worker;
+    std::vector<std::thread> workers;   // one dispatcher per slot
     bool stop = false;
     uint64_t next_id = 1;
-    uint64_t batches = 0, batched_reqs = 0, launches = 0;
+    std::atomic<uint64_t> batches{0}, batched_reqs{0}, launches{0};
     int min_batch = 1;        // static batching: start a slot only with this many pending
     double max_wait_s = 0;    // ... or once the oldest pending request waited this long
     // launch shape per (operation, level): Sign 8 warps per CTA, 4 per task
@@ -181,14 +184,21 @@ bool dispatch(dil_server *sv, Slot &s) {
             return false;   // static batching: wait for a fuller batch
         memcpy(warps, sv->warps, sizeof(warps));
         memcpy(wpt, sv->wpt, sizeof(wpt));
+        // continuous batching takes about a 1/S share of a backlog (at least 64)
+        size_t cap = (size_t)sv->max_batch;
+        if (sv->max_wait_s <= 0) {
+            const size_t share = (sv->pending.size() + sv->slots.size() - 1) / sv->slots.size();
+            cap = std::min(cap, std::max<size_t>(64, share));
+        }
         size_t bytes = 0;
-        while (!sv->pending.empty() && (int)s.reqs.size() < sv->max_batch) {
+        while (!sv->pending.empty() && s.reqs.size() < cap) {
             Req *r = sv->pending.front();
             if (bytes + r->mlen > sv->msg_cap && !s.reqs.empty()) break;   // waits for the next batch
             sv->pending.pop_front();
             bytes += r->mlen;
             s.reqs.push_back(r);
         }
+        if (!sv->pending.empty()) sv->cv_work.notify_one();   // another slot may take the rest
     }
     if (s.reqs.empty()) return false;
     // group by (op, level), stable within a group
@@ -291,30 +301,25 @@ void complete(dil_server *sv, Slot &s) {
     sv->cv_done.notify_all();
 }
 
-void worker_loop(dil_server *sv) {
+// Dispatcher of one slot: takes a batch, stages and launches it, waits for
+// its completion event and hands the results back; slots run in parallel, so
+// one slot's host-side copies do not hold up another's next batch.
+void slot_loop(dil_server *sv, Slot *s) {
     cudaSetDevice(sv->device);
     for (;;) {
-        bool progressed = false;
-        for (auto &s : sv->slots) {
-            if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
-                complete(sv, s);
-                progressed = true;
-            }
+        if (dispatch(sv, *s)) {
+            while (cudaEventQuery(s->done) == cudaErrorNotReady)
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+            complete(sv, *s);
+            continue;
         }
-        for (auto &s : sv->slots)
-            if (!s.busy && dispatch(sv, s)) progressed = true;
-        bool any_busy = false;
-        for (auto &s : sv->slots) any_busy |= s.busy;
         std::unique_lock<std::mutex> lk(sv->mu);
-        if (sv->stop && !any_busy && sv->pending.empty()) return;
-        if (!progressed) {
-            if (any_busy || !sv->pending.empty()) {   // kernels running, or a static batch filling up
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(10));
-            } else {
-                sv->cv_work.wait_for(lk, std::chrono::milliseconds(5),
-                                     [&] { return sv->stop || !sv->pending.empty(); });
-            }
+        if (sv->stop && sv->pending.empty()) return;
+        if (sv->pending.empty()) {
+            sv->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&] { return sv->stop || !sv->pending.empty(); });
+        } else {   // a static batch filling up
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     }
 }
@@ -366,7 +371,7 @@ int dil_server_create(int device, size_t memory_budget, int streams, int max_bat
             return DIL_ENOMEM;
         }
     }
-    sv->worker = std::thread(worker_loop, sv);
+    for (auto &s : sv->slots) sv->workers.emplace_back(slot_loop, sv, &s);
     *out = sv;
     return DIL_OK;
 }
@@ -378,7 +383,8 @@ int dil_server_destroy(dil_server *sv) {
         sv->stop = true;
         sv->cv_work.notify_all();
     }
-    if (sv->worker.joinable()) sv->worker.join();
+    for (auto &w : sv->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(sv->device);
     cudaDeviceSynchronize();
     for (auto &s : sv->slots) free_slot(s);
