@@ -135,7 +135,11 @@ typedef struct {
 
 /* Enqueues one persistent Sign launch on `stream` for njobs (1..3) jobs.  The
  * context's repetition cap (dil_set_max_iter) applies.  Uses the context's
- * workspace; calls on one context must not overlap on the GPU. */
+ * workspace; calls on one context must not overlap on the GPU.  The launch is
+ * asynchronous and reads the jobs' device buffers while it runs: they must
+ * stay allocated until the stream has passed the launch (the descriptors are
+ * copied, the buffers are not).  A CUDA graph of the launch is cached and
+ * replayed while the jobs' pointers and sizes are unchanged. */
 int dil_sign_persistent(dil_ctx *ctx, int njobs, const dil_sign_job *jobs, void *stream);
 
 /* Persistent launch shape: warps per CTA (1..8), warps per task group (1, 2
