@@ -286,6 +286,20 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK
     assert bool((status == 0).all())
     p_sign_ms = ranks.max(float(np.mean([e[0].elapsed_time(e[1]) for e in pev])))
+
+    # fusion ablation: the same Sign batch split into kernels (precompute + two per repetition round)
+    split_ms, rounds = [], 0
+    for i in range(2 + 5):
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        rounds = dil.dil_test_sign_split(ctx.handle, level, n, sk, msg, off, sig, status, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            split_ms.append(ev[0].elapsed_time(ev[1]))
+    assert bool((status == 0).all())
+    s_sign_ms = ranks.max(float(np.mean(split_ms)))
     served = served_summary(dev) if ranks.world == 1 else None
 
     # e2e: host buffers through the host-form C entry points
@@ -349,7 +363,9 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                   "persistent_sign_ops_s": ranks.world * n / (p_sign_ms * 1e-3),
                   "persistent_step_ops_s": ranks.world * n_ops / ((p_sign_ms + ranks.max(float(np.mean(ver_ms))))
                                                                   * 1e-3),
-                  "persistent_sign_ms": p_sign_ms},
+                  "persistent_sign_ms": p_sign_ms,
+                  "split_sign_ops_s": ranks.world * n / (s_sign_ms * 1e-3), "split_sign_rounds": rounds,
+                  "split_note": "fusion ablation: precompute kernel + two kernels per repetition round"},
         "served": served,
         "breakdown": {"sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
                       "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),

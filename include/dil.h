@@ -304,6 +304,18 @@ int dil_test_bounded_wait(dil_ctx *ctx, int flag_value, int limit, int *result);
  * (high, signed), 4 = warp shuffle.  Used for the integer roofline. */
 int dil_test_issue_rate(dil_ctx *ctx, int op, double *thread_ops_per_sm_clk);
 
+/* Test only (fusion ablation, section 4.2): Sign split into kernels instead
+ * of one fused kernel per task — a precompute kernel, then per repetition
+ * round one kernel for the first half (y, w, w1, c~ = H(mu || w1)) and one
+ * for the second (c, z, r0, hint, packing), with the per-task state in global
+ * memory and the host repeating rounds until no task is pending.  Same
+ * arguments and outputs as dil_sign_ex (signatures, status, repetitions
+ * equal the fused kernel's); `rounds` (nullable) returns the rounds run.
+ * Synchronous.  Uses the Sign launch shape with at most 2 warps per task. */
+int dil_test_sign_split(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+                        const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, int32_t *iterations,
+                        int *rounds, void *stream);
+
 /* Test only: throughput of the Keccak-f[1600] forms the kernels use (section
  * 3.3 of arXiv 2211.12265 describes the first), in SM clocks per state per
  * round, 32 warps per SM, every state independent.  form: 1 = one state on 25

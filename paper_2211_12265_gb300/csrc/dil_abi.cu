@@ -728,6 +728,40 @@ int dil_test_issue_rate(dil_ctx *c, int op, double *thread_ops_per_sm_clk) {
     return status_of(dil::measure_issue_rate(op, thread_ops_per_sm_clk));
 }
 
+int dil_test_sign_split(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+                        const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, int32_t *iterations,
+                        int *rounds, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level)) return DIL_EINVAL;
+    if (rounds) *rounds = 0;
+    if (n == 0) return DIL_OK;
+    if (!sk || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    const int l = level == 2 ? 4 : level == 3 ? 5 : 7, cap = (65536 - l) / l + 1;
+    const int max_iter = (c->max_iter > 0 && c->max_iter < cap) ? c->max_iter : cap;
+    const int p = std::min(c->wpt[1][lidx(level)], 2), w = std::max(c->warps[1][lidx(level)] / p * p, p);
+    const size_t per = dil::scratch_polys(dil::OP_SIGN, level) * POLY_BYTES + dil::split_state_bytes();
+    const size_t chunk = std::min<size_t>(n, (c->budget - 256) / per);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * per + 256);
+    if (rc) return rc;
+    int32_t *scratch = (int32_t *)c->ws;
+    void *state = (uint8_t *)c->ws + chunk * dil::scratch_polys(dil::OP_SIGN, level) * POLY_BYTES;
+    int *pending = (int *)((uint8_t *)state + chunk * dil::split_state_bytes());
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        const int m = (int)std::min(chunk, n - s0);
+        int r = 0;
+        cudaError_t e = dil::launch_sign_split(level, m, sk + skb * s0, msg, msg_off + s0, sig + sigb * s0,
+                                               task_status ? task_status + s0 : nullptr,
+                                               iterations ? iterations + s0 : nullptr, scratch, state, pending,
+                                               max_iter, w, p, (cudaStream_t)stream, &r);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (rounds) *rounds = std::max(*rounds, r);
+    }
+    return DIL_OK;
+}
+
 int dil_test_keccak_rate(dil_ctx *c, int form, double *sm_clocks_per_state_round) {
     TEST_PROLOGUE(c)
     if ((form != 1 && form != 2 && form != 6) || !sm_clocks_per_state_round) return DIL_EINVAL;

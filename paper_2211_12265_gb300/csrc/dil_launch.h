@@ -115,6 +115,10 @@ cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host);
 
 // test-only issue-rate probe (thread-ops per SM clock)
 cudaError_t measure_issue_rate(int op, double *rate);
+size_t split_state_bytes();
+cudaError_t launch_sign_split(int level, int n, const uint8_t *sk, const uint8_t *msg, const uint64_t *off,
+                              uint8_t *sig, int32_t *status, int32_t *iters, int32_t *scratch, void *state_mem,
+                              int *pending, int max_iter, int warps, int p, cudaStream_t s, int *rounds);
 cudaError_t measure_keccak_rate(int form, double *clk_per_state_round);
 
 }  // namespace dil

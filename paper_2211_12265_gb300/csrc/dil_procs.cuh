@@ -498,23 +498,22 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
     group_sync<P>(bar);
 }
 
-// One repetition of the rejection loop with nonce base kappa (l.6-18), with
-// early evaluation: each polynomial is checked as soon as it is produced.
-// Returns true (on every warp of the group) when (z, h) is accepted; then
-// gs.ctilde, scratch Z and gs.hmask hold the signature parts.
+// First half of one repetition of the rejection loop with nonce base kappa
+// (l.6-9): y, y^ = NTT(y), w = INTT(A^ o y^) (kept in scratch W), w1 and
+// c~ = H(mu || w1) into gs.ctilde; leaves gs.flag = 0 and gs.count = 0.
 // pre: the task's precomputation part (possibly prepared by another warp
 // group, so it is read through L2); itr: this worker's per-repetition part.
 // stop_below / rep: a speculative repetition rep of the persistent form
 // stops before hashing c~ once *stop_below (the smallest accepting repetition
-// found so far) is below rep; it then reports a rejection.
+// found so far) is below rep; it then returns false.
 template <int LEVEL, int P>
-__device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
-                             WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
-                             const int *stop_below = nullptr, int rep = 0) {
+__device__ bool sign_front(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
+                           WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
+                           const int *stop_below = nullptr, int rep = 0) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     volatile int *vflag = &gs.flag;
-    int32_t r[8], a[8], acc[8], ch[8];
+    int32_t r[8], a[8], acc[8];
     // y = ExpandMask(rho', kappa); y^ = NTT(y)  (l.6)
     if constexpr (P == 1)
         mask_stream<LEVEL>(gs.rhop, kappa, ms, itr + S::Y * N, itr + S::YH * N, ws, zt, lane);
@@ -562,7 +561,21 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskSt
         }
     }
     group_sync<P>(bar);
-    if (*vflag) return false;
+    return !*vflag;
+}
+
+// Second half (l.10-18), with early evaluation: each polynomial is checked as
+// soon as it is produced.  Needs gs.ctilde, gs.flag = gs.count = 0 and the
+// first half's scratch (y ring, W).  Returns true (on every warp of the group)
+// when (z, h) is accepted; then gs.ctilde, scratch Z and gs.hmask hold the
+// signature parts.
+template <int LEVEL, int P>
+__device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws,
+                          const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
+    using V = Lv<LEVEL>;
+    using S = Scratch<LEVEL>;
+    volatile int *vflag = &gs.flag;
+    int32_t r[8], a[8], ch[8];
     // c^ = NTT(SampleInBall(c~))  (l.10)
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta  (l.11, l.14)
@@ -646,6 +659,16 @@ __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskSt
     }
     group_sync<P>(bar);
     return !*vflag && gs.count <= V::OMEGA;
+}
+
+// One repetition (l.6-18): the two halves in one kernel.  Returns true when
+// (z, h) is accepted.
+template <int LEVEL, int P>
+__device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
+                             WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
+                             const int *stop_below = nullptr, int rep = 0) {
+    return sign_front<LEVEL, P>(kappa, pre, itr, ms, gs, ws, zt, izt, g, bar, lane, stop_below, rep) &&
+           sign_back<LEVEL, P>(kappa, pre, itr, gs, ws, zt, izt, g, bar, lane);
 }
 
 // Writes sig = c~ || z (gamma1 - z in ZBITS bits) || h (indices, then counts).

@@ -69,6 +69,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_rounding": [P, I, S, P, P, P, P, P],
                 "dil_test_issue_rate": [P, I, P],
                 "dil_test_keccak_rate": [P, I, P],
+                "dil_test_sign_split": [P, I, S, P, P, P, P, P, P, P, P],
                 "dil_test_bounded_wait": [P, I, I, P],
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
@@ -246,6 +247,16 @@ def dil_test_issue_rate(ctx, op: int) -> float:
     """Thread-ops per SM clock of one integer instruction class (see dil.h)."""
     r = ctypes.c_double()
     _check(load().dil_test_issue_rate(ctx, op, ctypes.byref(r)), "dil_test_issue_rate")
+    return r.value
+
+
+def dil_test_sign_split(ctx, level, n, sk, msg, msg_off, sig, task_status=None, iterations=None,
+                        stream=None) -> int:
+    """Sign split into kernels (fusion ablation; see dil.h); returns the rounds run."""
+    r = ctypes.c_int()
+    _check(load().dil_test_sign_split(ctx, level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(sig),
+                                      _ptr(task_status), _ptr(iterations), ctypes.byref(r), _stream(stream)),
+           "dil_test_sign_split")
     return r.value
 
 

@@ -222,3 +222,40 @@ def test_launch_shapes_bit_exact(orc, level, shape):
     assert np.array_equal(pk, opk) and np.array_equal(sk, osk)
     assert np.array_equal(sig, osig) and np.array_equal(it, oit) and np.array_equal(st, ost)
     assert np.array_equal(ok, orc.verify_batch(level, opk, msg, off, bad))
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_split_sign_equals_fused(orc, level):
+    """The fusion ablation (precompute kernel + two kernels per repetition
+    round) gives the fused kernel's signatures, statuses and repetition
+    counts, also under a repetition cap; sampled against the oracle."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    n = 613
+    seeds, msg, off = _batch(orc, level, n, 60 + level, "uniform", 0, 700)
+    c = dil.Context(0)
+    try:
+        c.apply_tuning()
+        _, sk = c.keygen(level, dev(seeds))
+        split = {}
+        for cap in (0, 3):
+            c.set_max_iter(cap)
+            fsig, fst, fit = c.sign(level, sk, dev(msg), dev(off), iterations=True)
+            ssig = torch.full_like(fsig, 0x33)
+            sst = torch.full_like(fst, 7)
+            sit = torch.zeros_like(fit)
+            rounds = dil.dil_test_sign_split(c.handle, level, n, sk, dev(msg), dev(off), ssig, sst, sit)
+            assert np.array_equal(host(ssig), host(fsig))
+            assert np.array_equal(host(sst), host(fst)) and np.array_equal(host(sit), host(fit))
+            assert rounds == int(host(fit).max())
+            if cap:
+                assert (host(fst) == dil.EITER).any() and (host(fst) == 0).any()
+            split[cap] = host(ssig)
+        c.set_max_iter(0)
+        skn = host(sk)
+    finally:
+        c.close()
+    for i in (0, n // 2, n - 1):
+        _, s, _ = orc.sign(level, skn[i].tobytes(), msg[off[i]:off[i + 1]].tobytes())
+        assert s == split[0][i].tobytes()
