@@ -339,6 +339,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     shfl_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["shfl"])
     peak = SMS * lop3_rate * SM_MAX_MHZ * 1e6 / 1e12
     traffic = load_traffic(level, n)
+    hbm = measured_hbm_gbs()
     table = autotune.load() or {}
     sign_p = table.get("plain", {}).get(str(level), {}).get("sign", {}).get("warps_per_task", 2)
 
@@ -379,6 +380,9 @@ def run_ours(args, ranks: Ranks) -> dict | None:
         "roofline": {"bound": "alu", "kernel": f"k_sign<{level}, {sign_p}>", "achieved": achieved,
                      "peak": peak, "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
                      "traffic": traffic, "ops_per_sign": ops / n,
+                     "dram_gbs": traffic / (sign_mean_ms * 1e-3) / 1e9 if traffic else None,
+                     "dram_frac_of_measured_hbm": (traffic / (sign_mean_ms * 1e-3) / 1e9 / hbm
+                                                   if traffic and hbm else None),
                      "peak_basis": f"{SMS} SMs x {lop3_rate:.1f} LOP3 thread-ops/SM/clk (measured live) x "
                                    f"{SM_MAX_MHZ:.0f} MHz max SM clock",
                      "shfl_thread_ops_per_sm_clk": shfl_rate},
@@ -508,6 +512,15 @@ def run_serving(args, ranks: Ranks) -> dict | None:
                                            "sweep": static}},
             "gpu_launches": launches,
             "gpu_launches_note": "keyed kernel launches of the warm-up, the saturated point and the continuous sweep"}
+
+
+def measured_hbm_gbs():
+    """Measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
 
 
 def load_traffic(level: int, n: int):
