@@ -64,7 +64,7 @@ int dil_ctx_create(int device, size_t workspace_budget, dil_ctx **out);
 /* Frees the workspace after synchronising the device.  NULL is accepted. */
 int dil_ctx_destroy(dil_ctx *ctx);
 
-/* Caps the number of Sign loop repetitions (Alg 2 l.5-19) for this context.
+/* Caps the number of Sign loop repetitions (Alg 2) for this context.
  * 0 restores the default cap implied by the 16-bit nonce (kappa + l - 1 <= 65535).
  * Tasks that reach the cap get DIL_EITER and an all-zero signature. */
 int dil_set_max_iter(dil_ctx *ctx, int max_iter);
@@ -157,8 +157,8 @@ int dil_persistent_status(dil_ctx *ctx, void *stream);
  * Resident keys (for serving many messages per key): a key store keeps, per
  * key, pk, sk (optional), tr = H(pk) and the key's precomputation (A^ =
  * ExpandA(rho), NTT(s1), NTT(s2), NTT(t0), NTT(t1 2^d)) on the device, so a
- * keyed Sign hashes only mu and rho' per message before its loop (Alg 2
- * l.1-2) and a keyed Verify skips ExpandA and H(pk) (Alg 3 l.1-2).  Outputs
+ * keyed Sign hashes only mu and rho' per message before its loop (Alg 2)
+ * and a keyed Verify skips ExpandA and H(pk) (Alg 3).  Outputs
  * equal dil_sign / dil_verify on the same keys and messages.
  * ------------------------------------------------------------------------- */
 typedef struct dil_keystore dil_keystore;

@@ -430,7 +430,7 @@ static void pointwise_acc(int32_t *acc, const int32_t *a, const int32_t *b)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Samplers (section 2.3; Alg 1 l.3-4; Alg 2 l.6, l.10)                      */
+/* Samplers (section 2.3; used by Alg 1 and Alg 2)                          */
 /* ------------------------------------------------------------------------ */
 /* ExpandA: A^_ij from SHAKE128(rho || j || i); rejection sampling keeps
  * 23-bit candidates below q ("Sampling", section 2.3; Alg 4 compares with q). */
@@ -775,25 +775,25 @@ static int unpack_hint(const params *p, const uint8_t *in, uint8_t *h)
 static void keygen(const params *p, const uint8_t seed[32], uint8_t *pk, uint8_t *sk)
 {
     uint8_t hb[128];
-    orc_shake256(seed, 32, hb, 128);                 /* Alg 1 l.2 */
+    orc_shake256(seed, 32, hb, 128);                 /* Alg 1: (rho, rho', K) = H(zeta) */
     const uint8_t *rho = hb, *rhop = hb + 32, *key = hb + 96;
     int32_t *A = malloc(sizeof(int32_t) * (size_t)p->k * p->l * N);
     int32_t s1[7 * N], s2[8 * N], s1h[7 * N], t[8 * N], t1[8 * N], t0[8 * N];
-    expand_a(p, rho, A);                             /* l.3 */
-    expand_s(p, rhop, s1, s2);                       /* l.4 */
+    expand_a(p, rho, A);                             /* A^ = ExpandA(rho) */
+    expand_s(p, rhop, s1, s2);                       /* (s1, s2) = ExpandS(rho') */
     for (int j = 0; j < p->l; j++) ntt(s1 + j * N, s1h + j * N);
-    for (int i = 0; i < p->k; i++) {                 /* l.5 */
+    for (int i = 0; i < p->k; i++) {                 /* t = INTT(A^ o NTT(s1)) + s2 */
         int32_t acc[N] = {0};
         for (int j = 0; j < p->l; j++) pointwise_acc(acc, A + ((size_t)i * p->l + j) * N, s1h + j * N);
         intt(acc, t + i * N);
         for (int c = 0; c < N; c++) t[i * N + c] = modq((int64_t)t[i * N + c] + s2[i * N + c]);
     }
-    for (int c = 0; c < p->k * N; c++) power2round(t[c], &t1[c], &t0[c]);   /* l.6 */
-    memcpy(pk, rho, 32);                              /* l.8 */
+    for (int c = 0; c < p->k * N; c++) power2round(t[c], &t1[c], &t0[c]);   /* (t1, t0) */
+    memcpy(pk, rho, 32);                              /* pk = rho || t1 */
     for (int i = 0; i < p->k; i++) pack_poly(t1 + i * N, 0, 1, 10, pk + 32 + i * (N * 10 / 8));
     uint8_t tr[32];
-    orc_shake256(pk, p->pk_bytes, tr, 32);           /* l.7 */
-    size_t eb = (size_t)N * p->eta_bits / 8;         /* l.9 */
+    orc_shake256(pk, p->pk_bytes, tr, 32);           /* tr = H(pk) */
+    size_t eb = (size_t)N * p->eta_bits / 8;
     memcpy(sk, rho, 32);
     memcpy(sk + 32, key, 32);
     memcpy(sk + 64, tr, 32);
@@ -837,45 +837,45 @@ static int sign(const params *p, const uint8_t *sk, const uint8_t *msg, size_t m
     if (max_iter <= 0 || max_iter > cap) max_iter = cap;
 
     unpack_sk(p, sk, f);
-    H2(f->tr, 32, msg, mlen, mu, 64);                 /* Alg 2 l.1 */
-    H2(f->key, 32, mu, 64, rhop, 64);                 /* l.2 */
-    expand_a(p, f->rho, A);                           /* l.3 */
-    for (int j = 0; j < p->l; j++) ntt(f->s1 + j * N, s1h + j * N);   /* l.4 */
+    H2(f->tr, 32, msg, mlen, mu, 64);                 /* Alg 2: mu = H(tr || M) */
+    H2(f->key, 32, mu, 64, rhop, 64);                 /* rho' = H(K || mu) */
+    expand_a(p, f->rho, A);                           /* A^ = ExpandA(rho) */
+    for (int j = 0; j < p->l; j++) ntt(f->s1 + j * N, s1h + j * N);
     for (int i = 0; i < p->k; i++) ntt(f->s2 + i * N, s2h + i * N);
     for (int i = 0; i < p->k; i++) ntt(f->t0 + i * N, t0h + i * N);
 
     int status = ORC_EITER, it;
     uint32_t kappa = 0;
-    for (it = 0; it < max_iter; it++, kappa += (uint32_t)p->l) {   /* l.5, l.19 */
+    for (it = 0; it < max_iter; it++, kappa += (uint32_t)p->l) {   /* rejection loop, kappa += l */
         t_cnt[4]++;
-        expand_mask(p, rhop, kappa, y);               /* l.6 */
+        expand_mask(p, rhop, kappa, y);               /* y = ExpandMask(rho', kappa) */
         for (int j = 0; j < p->l; j++) ntt(y + j * N, yh + j * N);
-        for (int i = 0; i < p->k; i++) {              /* l.7 */
+        for (int i = 0; i < p->k; i++) {
             int32_t acc[N] = {0};
             for (int j = 0; j < p->l; j++) pointwise_acc(acc, A + ((size_t)i * p->l + j) * N, yh + j * N);
             intt(acc, w + i * N);
         }
-        for (int c = 0; c < p->k * N; c++) w1[c] = highbits(2 * p->gamma2, w[c]);   /* l.8 */
+        for (int c = 0; c < p->k * N; c++) w1[c] = highbits(2 * p->gamma2, w[c]);   /* w1 = HighBits(w) */
         size_t w1b = (size_t)N * p->w1_bits / 8;
         uint8_t w1p[8 * N * 6 / 8];
         for (int i = 0; i < p->k; i++) pack_poly(w1 + i * N, 0, 1, p->w1_bits, w1p + i * w1b);
-        H2(mu, 64, w1p, (size_t)p->k * w1b, ctilde, 32);   /* l.9 */
+        H2(mu, 64, w1p, (size_t)p->k * w1b, ctilde, 32);   /* c~ = H(mu || w1) */
         int32_t c[N], ch[N];
-        sample_in_ball(p, ctilde, c);                 /* l.10 */
+        sample_in_ball(p, ctilde, c);                 /* c = SampleInBall(c~) */
         ntt(c, ch);
-        for (int j = 0; j < p->l; j++) {              /* l.11 */
+        for (int j = 0; j < p->l; j++) {              /* z = y + c s1 */
             for (int e = 0; e < N; e++) tmp[e] = modq((int64_t)ch[e] * s1h[j * N + e]);
             t_cnt[2] += N;
             intt(tmp, z + j * N);
             for (int e = 0; e < N; e++) z[j * N + e] = centred((int64_t)z[j * N + e] + y[j * N + e]);
         }
-        for (int i = 0; i < p->k; i++) {              /* l.12 */
+        for (int i = 0; i < p->k; i++) {              /* v_s = c s2 */
             for (int e = 0; e < N; e++) tmp[e] = modq((int64_t)ch[e] * s2h[i * N + e]);
             t_cnt[2] += N;
             intt(tmp, vs + i * N);
         }
-        int r0_fail_lit = 0, r0_fail_alt = 0;
-        for (int c2 = 0; c2 < p->k * N; c2++) {       /* l.13 */
+        int r0_fail_lit = 0, r0_fail_alt = 0;         /* r0 = LowBits(w - v_s), as printed */
+        for (int c2 = 0; c2 < p->k * N; c2++) {
             r0[c2] = lowbits(2 * p->gamma2, modq((int64_t)w[c2] - vs[c2]));
             int32_t lit = r0[c2] < 0 ? -r0[c2] : r0[c2];
             int32_t alt = lowbits(2 * p->gamma2, w[c2]) - centred(vs[c2]);
@@ -884,20 +884,20 @@ static int sign(const params *p, const uint8_t *sk, const uint8_t *msg, size_t m
             if (alt >= p->gamma2 - p->beta) r0_fail_alt = 1;
         }
         if (r0_fail_lit != r0_fail_alt) t_cnt[5]++;
-        int reject = norm_inf(z, (size_t)p->l * N) >= p->gamma1 - p->beta || r0_fail_lit;   /* l.14 */
+        int reject = norm_inf(z, (size_t)p->l * N) >= p->gamma1 - p->beta || r0_fail_lit;
         if (!reject) {
-            for (int i = 0; i < p->k; i++) {          /* l.17 */
+            for (int i = 0; i < p->k; i++) {          /* v_t = c t0 */
                 for (int e = 0; e < N; e++) tmp[e] = modq((int64_t)ch[e] * t0h[i * N + e]);
                 t_cnt[2] += N;
                 intt(tmp, vt + i * N);
             }
-            int count = 0;
-            for (int c2 = 0; c2 < p->k * N; c2++) {   /* l.18 */
+            int count = 0;                            /* h = MakeHint(-v_t, w - v_s + v_t) */
+            for (int c2 = 0; c2 < p->k * N; c2++) {
                 int32_t rr = modq((int64_t)w[c2] - vs[c2] + vt[c2]);
                 h[c2] = (uint8_t)make_hint(2 * p->gamma2, modq(-(int64_t)vt[c2]), rr);
                 count += h[c2];
             }
-            if (norm_inf(vt, (size_t)p->k * N) >= p->gamma2 || count > p->omega) reject = 1;   /* l.19 */
+            if (norm_inf(vt, (size_t)p->k * N) >= p->gamma2 || count > p->omega) reject = 1;
         }
         if (!reject) {
             size_t zb = (size_t)N * p->z_bits / 8;
@@ -941,17 +941,17 @@ static int verify(const params *p, const uint8_t *pk, const uint8_t *msg, size_t
     for (int i = 0; i < p->k; i++) unpack_poly(pk + 32 + i * (N * 10 / 8), 0, 1, 10, t1 + i * N);
     for (int j = 0; j < p->l; j++) unpack_poly(sig + 32 + j * zb, p->gamma1, -1, p->z_bits, z + j * N);
     if (!unpack_hint(p, sig + 32 + p->l * zb, h)) ok = 0;
-    if (ok && norm_inf(z, (size_t)p->l * N) >= p->gamma1 - p->beta) ok = 0;   /* Alg 3 l.6, first term */
+    if (ok && norm_inf(z, (size_t)p->l * N) >= p->gamma1 - p->beta) ok = 0;   /* Alg 3: z norm check */
     if (ok) {
-        expand_a(p, pk, A);                           /* l.1 */
+        expand_a(p, pk, A);                           /* A^ = ExpandA(rho) */
         uint8_t tr[32], mu[64], c2[32];
-        orc_shake256(pk, p->pk_bytes, tr, 32);         /* l.2 */
-        H2(tr, 32, msg, mlen, mu, 64);
+        orc_shake256(pk, p->pk_bytes, tr, 32);
+        H2(tr, 32, msg, mlen, mu, 64);                /* mu = H(H(pk) || M) */
         int32_t c[N], ch[N];
-        sample_in_ball(p, sig, c);                    /* l.3 */
+        sample_in_ball(p, sig, c);                    /* c = SampleInBall(c~) */
         ntt(c, ch);
         for (int j = 0; j < p->l; j++) ntt(z + j * N, zh + j * N);
-        for (int i = 0; i < p->k; i++) {              /* l.4 */
+        for (int i = 0; i < p->k; i++) {              /* v = A z - c t1 2^d */
             int32_t acc[N] = {0}, t1s[N], t1h[N];
             for (int j = 0; j < p->l; j++) pointwise_acc(acc, A + ((size_t)i * p->l + j) * N, zh + j * N);
             for (int e = 0; e < N; e++) t1s[e] = modq((int64_t)t1[i * N + e] << D);
@@ -961,7 +961,7 @@ static int verify(const params *p, const uint8_t *pk, const uint8_t *msg, size_t
             intt(acc, v + i * N);
         }
         int count = 0;
-        for (int e = 0; e < p->k * N; e++) {          /* l.5 */
+        for (int e = 0; e < p->k * N; e++) {          /* w1' = UseHint(h, v) */
             w1[e] = use_hint(2 * p->gamma2, h[e], v[e]);
             count += h[e];
         }
@@ -969,7 +969,7 @@ static int verify(const params *p, const uint8_t *pk, const uint8_t *msg, size_t
         uint8_t w1p[8 * N * 6 / 8];
         for (int i = 0; i < p->k; i++) pack_poly(w1 + i * N, 0, 1, p->w1_bits, w1p + i * w1b);
         H2(mu, 64, w1p, (size_t)p->k * w1b, c2, 32);
-        if (memcmp(c2, sig, 32) != 0) ok = 0;          /* l.6 */
+        if (memcmp(c2, sig, 32) != 0) ok = 0;          /* c~ == H(mu || w1') */
         if (count > p->omega) ok = 0;
     }
     free(A);

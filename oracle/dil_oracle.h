@@ -47,7 +47,7 @@ void orc_poly_mul(const int32_t a[256], const int32_t b[256], int32_t c[256]);
 /* selects which NTT form the procedures use: 0 = fast (default), 1 = definition */
 void orc_use_def_ntt(int on);
 
-/* Samplers (section 2.3; Alg 1 l.3-4, Alg 2 l.6 and l.10). */
+/* Samplers (section 2.3; Alg 1 and Alg 2). */
 int orc_expand_a(int level, const uint8_t rho[32], int32_t *ahat /* k*l*256 */);
 int orc_expand_s(int level, const uint8_t rhop[64], int32_t *s1 /* l*256 */, int32_t *s2 /* k*256 */);
 int orc_expand_mask(int level, const uint8_t rhop[64], uint32_t kappa, int32_t *y /* l*256 */);

@@ -305,7 +305,7 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
                          int lane) {
     using V = Lv<LEVEL>;
     int32_t r[8], a[8], acc[8];
-    // (rho, rho', K) = H(zeta)  (Alg 1 l.2)
+    // (rho, rho', K) = H(zeta)  (Alg 1)
     if (g == 0) {
         stage_bytes(gs.hb, seed, 32, lane);
         __syncwarp();
@@ -322,7 +322,7 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
         gs.rhop[32 + lane] = gs.hb[64 + lane];
     }
     group_sync<P>(bar);
-    // s1: sample, pack into sk, NTT  (l.4)
+    // s1: sample, pack into sk, NTT
     constexpr int U1 = Units<V::L, P>::SIZE;
 #pragma unroll 1
     for (int j = U1 * g; j < V::L; j += U1 * P) {
@@ -343,11 +343,11 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
             store_l2(scratch + jj * N, r, lane);
         }
     }
-    // A^ = ExpandA(rho) into scratch after s^1  (l.3)
+    // A^ = ExpandA(rho) into scratch after s^1
     constexpr int KL = V::K * V::L;
     expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
     group_sync<P>(bar);
-    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)  (l.3, l.5, l.6)
+    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)
 #pragma unroll 1
     for (int i = g; i < V::K; i += P) {
         accumulate_row(acc, scratch + (V::L + i * V::L) * N, V::L, scratch, lane);
@@ -375,7 +375,7 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
     }
     __threadfence_block();
     group_sync<P>(bar);
-    // tr = H(rho || t1)  (l.7)
+    // tr = H(rho || t1)
     if (g == 0) {
         uint32_t lo = 0, hi = 0;
         absorb_concat(lo, hi, gs.hb, 0, pk, V::PK, 136, lane);
@@ -405,22 +405,22 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
     }
     group_sync<P>(bar);
     if (g == 0) {
-        // mu = H(tr || M)  (Alg 2 l.1)
+        // mu = H(tr || M)  (Alg 2)
         uint32_t lo = 0, hi = 0;
         absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
         squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
         __syncwarp();
-        // rho' = H(K || mu)  (l.2)
+        // rho' = H(K || mu)
         lo = 0;
         hi = 0;
         absorb_smem(lo, hi, gs.hb + HB_K, 96, 136, lane);
         squeeze_words(lo, hi, gs.rhop, 8, lane);
         __syncwarp();
     }
-    // A^ = ExpandA(rho)  (l.3)
+    // A^ = ExpandA(rho)
     constexpr int KL = V::K * V::L;
     expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, ws, lane);
-    // s^1, s^2, t^0  (l.4): polynomials u = 0 .. l + 2k - 1 across the group
+    // s^1, s^2, t^0: polynomials u = 0 .. l + 2k - 1 across the group
 #pragma unroll 1
     for (int u = g; u < V::L + 2 * V::K; u += P) {
         if (u < V::L) {
@@ -498,8 +498,8 @@ __device__ void key_prepare(const uint8_t *__restrict__ pk, const uint8_t *__res
     group_sync<P>(bar);
 }
 
-// First half of one repetition of the rejection loop with nonce base kappa
-// (l.6-9): y, y^ = NTT(y), w = INTT(A^ o y^) (kept in scratch W), w1 and
+// First half of one repetition of the rejection loop of Alg 2 with nonce
+// base kappa: y, y^ = NTT(y), w = INTT(A^ o y^) (kept in scratch W), w1 and
 // c~ = H(mu || w1) into gs.ctilde; leaves gs.flag = 0 and gs.count = 0.
 // pre: the task's precomputation part (possibly prepared by another warp
 // group, so it is read through L2); itr: this worker's per-repetition part.
@@ -514,14 +514,14 @@ __device__ bool sign_front(int kappa, const int32_t *pre, int32_t *itr, MaskStre
     using S = Scratch<LEVEL>;
     volatile int *vflag = &gs.flag;
     int32_t r[8], a[8], acc[8];
-    // y = ExpandMask(rho', kappa); y^ = NTT(y)  (l.6)
+    // y = ExpandMask(rho', kappa); y^ = NTT(y)
     if constexpr (P == 1)
         mask_stream<LEVEL>(gs.rhop, kappa, ms, itr + S::Y * N, itr + S::YH * N, ws, zt, lane);
     else
         expand_mask_range<LEVEL>(gs.rhop, kappa, share_lo<V::L, P>(g), share_lo<V::L, P>(g + 1), itr + S::Y * N,
                                  itr + S::YH * N, ws, zt, lane);
     group_sync<P>(bar);
-    // w = INTT(A^ o y^); w1 = HighBits(w)  (l.7-8)
+    // w = INTT(A^ o y^); w1 = HighBits(w)
 #pragma unroll 1
     for (int i = g; i < V::K; i += P) {
 #pragma unroll
@@ -546,7 +546,7 @@ __device__ bool sign_front(int kappa, const int32_t *pre, int32_t *itr, MaskStre
         pack_seq<V::W1BITS>(gs.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
     }
     group_sync<P>(bar);
-    // c~ = H(mu || w1)  (l.9)
+    // c~ = H(mu || w1)
     if (g == 0) {
         int stop = 0;
         if (stop_below) stop = __shfl_sync(FULL, lane == 0 ? (int)(__ldcg(stop_below) < rep) : 0, 0);
@@ -564,11 +564,11 @@ __device__ bool sign_front(int kappa, const int32_t *pre, int32_t *itr, MaskStre
     return !*vflag;
 }
 
-// Second half (l.10-18), with early evaluation: each polynomial is checked as
-// soon as it is produced.  Needs gs.ctilde, gs.flag = gs.count = 0 and the
-// first half's scratch (y ring, W).  Returns true (on every warp of the group)
-// when (z, h) is accepted; then gs.ctilde, scratch Z and gs.hmask hold the
-// signature parts.
+// Second half of the repetition, with early evaluation: each polynomial is
+// checked as soon as it is produced.  Needs gs.ctilde, gs.flag = gs.count = 0
+// and the first half's scratch (y ring, W).  Returns true (on every warp of
+// the group) when (z, h) is accepted; then gs.ctilde, scratch Z and gs.hmask
+// hold the signature parts.
 template <int LEVEL, int P>
 __device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws,
                           const int32_t *zt, const int32_t *izt, int g, int bar, int lane) {
@@ -576,9 +576,9 @@ __device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem
     using S = Scratch<LEVEL>;
     volatile int *vflag = &gs.flag;
     int32_t r[8], a[8], ch[8];
-    // c^ = NTT(SampleInBall(c~))  (l.10)
+    // c^ = NTT(SampleInBall(c~))
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
-    // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta  (l.11, l.14)
+    // z = y + INTT(c^ o s^1); reject if ||z|| >= gamma1 - beta
 #pragma unroll 1
     for (int j = g; j < V::L && !*vflag; j += P) {
         load_l2_cg(a, pre + (S::S1H + j) * N, lane);
@@ -598,7 +598,7 @@ __device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem
         }
         store_l0(itr + (S::Z + j) * N, r, lane);
     }
-    // v_s = INTT(c^ o s^2); r0 = LowBits(w - v_s)  (l.12-14)
+    // v_s = INTT(c^ o s^2); r0 = LowBits(w - v_s)
 #pragma unroll 1
     for (int i = g; i < V::K && !*vflag; i += P) {
         load_l2_cg(a, pre + (S::S2H + i) * N, lane);
@@ -625,7 +625,7 @@ __device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem
     }
     group_sync<P>(bar);
     if (*vflag) return false;
-    // v_t = INTT(c^ o t^0); h = MakeHint(-v_t, w - v_s + v_t)  (l.17-19)
+    // v_t = INTT(c^ o t^0); h = MakeHint(-v_t, w - v_s + v_t)
 #pragma unroll 1
     for (int i = g; i < V::K && !*vflag; i += P) {
         load_l2_cg(a, pre + (S::T0H + i) * N, lane);
@@ -661,7 +661,7 @@ __device__ bool sign_back(int kappa, const int32_t *pre, int32_t *itr, GroupSmem
     return !*vflag && gs.count <= V::OMEGA;
 }
 
-// One repetition (l.6-18): the two halves in one kernel.  Returns true when
+// One repetition: the two halves in one kernel.  Returns true when
 // (z, h) is accepted.
 template <int LEVEL, int P>
 __device__ bool sign_attempt(int kappa, const int32_t *pre, int32_t *itr, MaskStream &ms, GroupSmem &gs,
@@ -750,7 +750,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     }
     group_sync<P>(bar);
     if (*vflag) return 0;
-    // z: unpack, ||z|| < gamma1 - beta, z^ = NTT(z)  (Alg 3 l.6 first term, l.4)
+    // z: unpack, ||z|| < gamma1 - beta, z^ = NTT(z)  (Alg 3)
 #pragma unroll 1
     for (int j = g; j < V::L && !*vflag; j += P) {
         unpack_poly_l0<V::ZBITS>(r, sig + V::SIG_Z + j * V::POLYZ, V::GAMMA1, ws, lane);
@@ -768,7 +768,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     constexpr int KL = V::K * V::L;
     if (!KEYED)
         expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
-    // mu = H(H(rho || t1) || M)  (l.2), on the last warp
+    // mu = H(H(rho || t1) || M), on the last warp
     if (g == P - 1) {
         uint32_t lo = 0, hi = 0;
         if (KEYED) {
@@ -785,9 +785,9 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     }
     group_sync<P>(bar);
     if (*vflag) return 0;
-    // c^ = NTT(SampleInBall(c~))  (l.3)
+    // c^ = NTT(SampleInBall(c~))
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
-    // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)  (l.4-5)
+    // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)
     using S = Scratch<LEVEL>;
     const int32_t *ahat = KEYED ? key + S::AH * N : scratch + V::L * N;
 #pragma unroll 1
@@ -813,7 +813,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         pack_seq<V::W1BITS>(gs.hb + HB_W1 + i * V::POLYW1, r, 0, 1, lane);
     }
     group_sync<P>(bar);
-    // c~ == H(mu || w1')  (l.6)
+    // c~ == H(mu || w1')
     if (g == 0) {
         uint32_t lo = 0, hi = 0;
         absorb_smem(lo, hi, gs.hb + HB_MU, 64 + V::K * V::POLYW1, 136, lane);

@@ -4,7 +4,7 @@ Counts what the algorithm itself requires, independent of how a kernel does
 it: Keccak-f[1600] permutations, NTT/INTT butterflies (1024 per 256-point
 transform), pointwise products mod q, and sampled or (un)packed coefficients.
 Sign's count depends on the number of loop repetitions per task, which the
-engine reports (``dil_sign_ex``); the masking term (Alg 2 l.17-19) is counted
+engine reports (``dil_sign_ex``); the masking term (Alg 2) is counted
 once per task, for the accepted repetition, so the figure is a lower bound.
 
 ``int_ops`` converts the counts to 32-bit integer operations with fixed

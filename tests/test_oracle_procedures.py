@@ -1,9 +1,9 @@
 """Pins the oracle's Alg 1 (Gen), Alg 2 (Sign) and Alg 3 (Verify).
 
 * Verify(Sign(m)) accepts; every single-bit flip of the signature, public key
-  or message is rejected (Alg 3 l.6).
+  or message is rejected (Alg 3).
 * Gen's public and secret key satisfy t = A s1 + s2 with A s1 computed by the
-  schoolbook product, and (t1, t0) = Power2Round(t) (Alg 1 l.5-6).
+  schoolbook product, and (t1, t0) = Power2Round(t) (Alg 1).
 * A second Verify, written here with schoolbook products and the closed-form
   rounding, accepts the oracle's signatures (Alg 3).
 * The mean number of Sign loop repetitions matches the values the paper prints

@@ -1,4 +1,4 @@
-"""Pins the oracle's samplers (section 2.3; Alg 1 l.3-4, Alg 2 l.6, l.10).
+"""Pins the oracle's samplers (section 2.3; Alg 1 and Alg 2).
 
 Each sampler is re-derived here from a hashlib SHAKE stream (a second,
 independent reading of the same definition) and its output ranges and

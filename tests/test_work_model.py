@@ -23,7 +23,7 @@ def test_sign_and_verify_counts(orc, level):
     assert w["coefficients"] == c["coefficients"]
     # permutations: SampleInBall / ExpandA may rarely squeeze one more block
     assert w["permutations"] <= c["permutations"] <= w["permutations"] * 1.01
-    # the masking term (Alg 2 l.17) is counted once per task by the model,
+    # the masking term (Alg 2) is counted once per task by the model,
     # for every iteration that passes the first checks by the oracle
     assert w["butterflies"] <= c["butterflies"] <= w["butterflies"] * 1.10
     assert w["pointwise"] <= c["pointwise"] <= w["pointwise"] * 1.10
