@@ -199,7 +199,8 @@ typedef struct {
     uint64_t id;
     int32_t op;          /* 0 = sign, 1 = verify */
     int32_t level;
-    int32_t status;      /* sign: DIL_OK, DIL_EITER or DIL_EINVAL (unknown key) */
+    int32_t status;      /* sign: DIL_OK, DIL_EITER or DIL_EINVAL (unknown key); any op:
+                            DIL_ECUDA when the batch's copies or kernels failed */
     uint8_t ok;          /* verify: 1 = accept */
     uint8_t sig[4595];   /* sign: the signature (first SIG bytes) */
     double latency_s;    /* arrival to result visible on the host */

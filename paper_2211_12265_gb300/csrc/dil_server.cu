@@ -83,6 +83,7 @@ struct Slot {
     cudaStream_t gstream[MAX_GROUPS] = {};  // one per group of a batch
     cudaEvent_t done = nullptr, ev_in = nullptr, ev_grp[MAX_GROUPS] = {};
     bool busy = false;
+    bool failed = false;   // a copy, launch or the batch's kernels failed: its requests report DIL_ECUDA
     uint8_t *d_msg = nullptr, *d_sig_in = nullptr, *d_sig_out = nullptr, *d_ok = nullptr;
     uint64_t *d_off = nullptr;
     int32_t *d_key = nullptr, *d_status = nullptr, *d_scratch = nullptr;
@@ -228,37 +229,42 @@ bool dispatch(dil_server *sv, Slot &s) {
     s.sig_used = sig_off;
     const size_t n = s.reqs.size();
     cudaStream_t st = s.stream;
-    cudaMemcpyAsync(s.d_key, s.h_key, n * 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s.d_off, s.h_off, noff * 8, cudaMemcpyHostToDevice, st);
-    if (mbytes) cudaMemcpyAsync(s.d_msg, s.h_msg, mbytes, cudaMemcpyHostToDevice, st);
+    cudaError_t err = cudaSuccess;
+    auto check = [&err](cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    };
+    check(cudaMemcpyAsync(s.d_key, s.h_key, n * 4, cudaMemcpyHostToDevice, st));
+    check(cudaMemcpyAsync(s.d_off, s.h_off, noff * 8, cudaMemcpyHostToDevice, st));
+    if (mbytes) check(cudaMemcpyAsync(s.d_msg, s.h_msg, mbytes, cudaMemcpyHostToDevice, st));
     bool any_verify = false;
     for (auto &g : s.groups) any_verify |= g.op == 1;
-    if (any_verify) cudaMemcpyAsync(s.d_sig_in, s.h_sig_in, sig_off, cudaMemcpyHostToDevice, st);
-    cudaEventRecord(s.ev_in, st);
+    if (any_verify) check(cudaMemcpyAsync(s.d_sig_in, s.h_sig_in, sig_off, cudaMemcpyHostToDevice, st));
+    check(cudaEventRecord(s.ev_in, st));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
         const Group &g = s.groups[gi];
         const int li = level_slot(g.level);
         dil_keystore *ks = sv->ks[li];
         int32_t *scratch = s.d_scratch + (size_t)g.first * max_task_polys() * 256;
         cudaStream_t gs = s.gstream[gi];
-        cudaStreamWaitEvent(gs, s.ev_in, 0);
+        check(cudaStreamWaitEvent(gs, s.ev_in, 0));
         if (g.op == 0) {
             const int l = g.level == 2 ? 4 : g.level == 3 ? 5 : 7;
-            dil::launch_sign_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->sk, ks->keys, s.d_msg,
+            check(dil::launch_sign_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->sk, ks->keys, s.d_msg,
                                    s.d_off + g.off_first, s.d_sig_out + g.sig_first, s.d_status + g.first, nullptr,
-                                   scratch, (65536 - l) / l + 1, warps[0][li], wpt[0][li], gs);
+                                   scratch, (65536 - l) / l + 1, warps[0][li], wpt[0][li], gs));
         } else {
-            dil::launch_verify_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->pk, ks->keys, ks->tr,
+            check(dil::launch_verify_keyed(g.level, g.count, sv->nkeys[li], s.d_key + g.first, ks->pk, ks->keys, ks->tr,
                                      s.d_msg, s.d_off + g.off_first, s.d_sig_in + g.sig_first, s.d_ok + g.first,
-                                     scratch, warps[1][li], wpt[1][li], gs);
+                                     scratch, warps[1][li], wpt[1][li], gs));
         }
-        cudaEventRecord(s.ev_grp[gi], gs);
-        cudaStreamWaitEvent(st, s.ev_grp[gi], 0);
+        check(cudaEventRecord(s.ev_grp[gi], gs));
+        check(cudaStreamWaitEvent(st, s.ev_grp[gi], 0));
     }
-    cudaMemcpyAsync(s.h_sig_out, s.d_sig_out, sig_off, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(s.h_status, s.d_status, n * 4, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(s.h_ok, s.d_ok, n, cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(s.done, st);
+    check(cudaMemcpyAsync(s.h_sig_out, s.d_sig_out, sig_off, cudaMemcpyDeviceToHost, st));
+    check(cudaMemcpyAsync(s.h_status, s.d_status, n * 4, cudaMemcpyDeviceToHost, st));
+    check(cudaMemcpyAsync(s.h_ok, s.d_ok, n, cudaMemcpyDeviceToHost, st));
+    check(cudaEventRecord(s.done, st));
+    s.failed = err != cudaSuccess;
     s.busy = true;
     sv->batches++;
     sv->launches += s.groups.size();
@@ -275,7 +281,11 @@ void complete(dil_server *sv, Slot &s) {
             const size_t sb = sig_bytes(r->level);
             r->res.status = 0;
             r->res.ok = 0;
-            if (g.op == 0) {
+            if (s.failed) {
+                r->res.status = DIL_ECUDA;
+                if (g.op == 0 && r->status) *r->status = DIL_ECUDA;
+                if (g.op == 1 && r->ok) *r->ok = 0;
+            } else if (g.op == 0) {
                 r->res.status = s.h_status[i];
                 if (r->status) *r->status = s.h_status[i];
                 if (r->sig_out) memcpy(r->sig_out, s.h_sig_out + so, sb);
@@ -308,8 +318,10 @@ void slot_loop(dil_server *sv, Slot *s) {
     cudaSetDevice(sv->device);
     for (;;) {
         if (dispatch(sv, *s)) {
-            while (cudaEventQuery(s->done) == cudaErrorNotReady)
+            cudaError_t q;
+            while ((q = cudaEventQuery(s->done)) == cudaErrorNotReady)
                 std::this_thread::sleep_for(std::chrono::microseconds(5));
+            if (q != cudaSuccess) s->failed = true;
             complete(sv, *s);
             continue;
         }
