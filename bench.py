@@ -200,9 +200,17 @@ def cpu_baseline(level: int, wl: dict, budget_s: float = 15.0) -> dict:
         t_total += time.perf_counter() - t0
         done += sample
         assert ok.all()
+    # one host thread on a smaller sample (a few seconds)
+    one = min(sample, 16)
+    t0 = time.perf_counter()
+    sig1, _, _ = oracle.sign_batch(level, sk[:one], msg, off[: one + 1], nthreads=1)
+    ok1 = oracle.verify_batch(level, pk[:one], msg, off[: one + 1], sig1, nthreads=1)
+    t1 = time.perf_counter() - t0
+    assert ok1.all()
     return {"value": 2 * done / t_total, "unit": "ops/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} Dilithium{level} sign+verify tasks ({sample} distinct, messages "
-                      f"{int(lens.min())}-{int(lens.max())} B) in {t_total:.1f} s"}
+                      f"{int(lens.min())}-{int(lens.max())} B) in {t_total:.1f} s",
+            "single_thread": {"value": 2 * one / t1, "unit": "ops/s", "sample": f"{one} sign+verify tasks"}}
 
 
 # ----------------------------------------------------------------- ours
