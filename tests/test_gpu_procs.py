@@ -110,6 +110,31 @@ def test_empty_and_single(ctx, orc):
     assert gpu_verify(ctx, level, pk, msg, off, sig)[0] == 1
 
 
+@pytest.mark.parametrize("level", [2, 5])
+def test_long_and_empty_messages(ctx, orc, level):
+    """Messages of 0 bytes, exactly one and two SHAKE256 blocks around the mu
+    hash's boundaries, and 64 KB / 1 MB, mixed in one batch: signatures equal
+    the oracle's and all verify; a flipped byte at the end of the longest
+    message is rejected."""
+    from gpu_util import gpu_keygen, gpu_sign, gpu_verify
+    lens = np.array([0, 1, 72, 103, 104, 135, 136, 239, 240, 65536, 1 << 20, 0, 5], dtype=np.int64)
+    n = lens.size
+    rng = np.random.default_rng(31)
+    msg = rng.integers(0, 256, int(lens.sum()) + 1, dtype=np.uint8)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    seeds = W.seeds(n, 70 + level)
+    pk, sk = gpu_keygen(ctx, level, seeds)
+    sig, st, _ = gpu_sign(ctx, level, sk, msg, off)
+    osig, ost, _ = orc.sign_batch(level, sk, msg, off)
+    assert np.array_equal(sig, osig) and (st == 0).all()
+    assert gpu_verify(ctx, level, pk, msg, off, sig).all()
+    bad = msg.copy()
+    bad[int(off[11]) - 1] ^= 0x80                       # last byte of the 1 MB message
+    ok = gpu_verify(ctx, level, pk, bad, off, sig)
+    assert not ok[10] and ok[:10].all() and ok[11:].all()
+
+
 def test_iteration_cap(ctx, orc):
     from gpu_util import gpu_sign
     level = 2
