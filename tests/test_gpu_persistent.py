@@ -53,7 +53,7 @@ def _persistent(torch, ctx, jobs, reps=1):
 
 
 @pytest.mark.parametrize("tuning", [(8, 2, 0, 1, 4), (4, 1, 0, 1, 0), (4, 1, 0, 3, 2), (8, 4, 2, 2, 8),
-                                    (2, 2, 1, 1, 1)])
+                                    (2, 2, 1, 1, 1), (8, 1, 0, 1, 8), (1, 1, 0, 1, 16)])
 def test_single_job_matches_plain(torch_cuda, tuning):
     from paper_2211_12265_gb300 import dil
     j = _job_inputs(torch_cuda, 2, 700, 31)
