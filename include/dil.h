@@ -19,8 +19,11 @@
  *     task-major and densely packed (task i's pk starts at pk + i * PK).
  *     Messages are one concatenated byte array `msg` with n + 1 byte offsets
  *     `msg_off` (task i's message is msg[msg_off[i] .. msg_off[i+1]) and may be
- *     empty; msg may be NULL when every message is empty).  No alignment is
- *     required.
+ *     empty; msg may be NULL when every message is empty).  Offsets must not
+ *     decrease: a task whose offsets do (device arrays are not read on the
+ *     host) is rejected by the kernels — Sign writes status DIL_EINVAL and a
+ *     zeroed signature, Verify ok = 0 — and the host-buffer forms return
+ *     DIL_EINVAL.  No alignment is required.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
  *     asynchronous on that stream: the return value reports argument and
  *     launch errors only; per-task results are written to device memory.

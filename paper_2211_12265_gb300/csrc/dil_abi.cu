@@ -549,6 +549,14 @@ int run_pipeline(dil_ctx *c, size_t n, size_t per_task, cudaStream_t s0, Chunk c
     return e == cudaSuccess ? DIL_OK : DIL_ECUDA;
 }
 
+// Host offsets of the host forms: non-decreasing (a task's message is
+// msg[off[i] .. off[i + 1])).
+bool offsets_ok(const uint64_t *off, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (off[i + 1] < off[i]) return false;
+    return true;
+}
+
 bool h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
 }
@@ -595,7 +603,7 @@ int dil_sign_host(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint
     size_t pkb, skb, sigb;
     sizes_of(level, pkb, skb, sigb);
     const size_t mlen = (size_t)msg_off[n];
-    if (mlen && !msg) return DIL_EINVAL;
+    if ((mlen && !msg) || !offsets_ok(msg_off, n)) return DIL_EINVAL;
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
     int rc = ensure_stage(c, al(skb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(4 * n));
@@ -634,7 +642,7 @@ int dil_verify_host(dil_ctx *c, int level, size_t n, const uint8_t *pk, const ui
     size_t pkb, skb, sigb;
     sizes_of(level, pkb, skb, sigb);
     const size_t mlen = (size_t)msg_off[n];
-    if (mlen && !msg) return DIL_EINVAL;
+    if ((mlen && !msg) || !offsets_ok(msg_off, n)) return DIL_EINVAL;
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
     int rc = ensure_stage(c, al(pkb * n) + al(mlen + 1) + al(8 * (n + 1)) + al(sigb * n) + al(n));

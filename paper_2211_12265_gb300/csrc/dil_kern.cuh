@@ -3,6 +3,7 @@
 // holds W warps = W / P task groups of P warps; the CTA shares the NTT twiddle
 // tables in shared memory, each group its GroupSmem, each warp its WarpSmem.
 #pragma once
+#include "../../include/dil.h"
 #include "dil_launch.h"
 #include "dil_procs.cuh"
 

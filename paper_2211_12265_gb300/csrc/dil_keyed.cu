@@ -33,18 +33,19 @@ __global__ void __launch_bounds__(256, 4) k_sign_keyed(int n, int n_keys, const 
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     const int key = key_idx[task];
-    if (key < 0 || key >= n_keys) {   // unknown key: reject the task, touch nothing else
+    uint64_t m0;
+    size_t mlen;
+    if (key < 0 || key >= n_keys || !message_of(off, task, m0, mlen)) {   // unknown key or bad offsets: reject
         sign_zero<LEVEL, P>(sig + (size_t)task * V::SIG, v.g, v.lane);
         if (v.g == 0 && v.lane == 0) {
-            if (status) status[task] = -1;
+            if (status) status[task] = DIL_EINVAL;
             if (iters) iters[task] = 0;
         }
         return;
     }
     const int32_t *pre = keys + (size_t)key * S::KEY_POLYS * N;
     int32_t *itr = scratch + (size_t)task * S::ITR_POLYS * N;
-    const uint64_t m0 = off[task], m1 = off[task + 1];
-    sign_prepare_keyed<LEVEL, P>(sk + (size_t)key * V::SK, msg + m0, (size_t)(m1 - m0), *v.gs, v.g, v.bar, v.lane);
+    sign_prepare_keyed<LEVEL, P>(sk + (size_t)key * V::SK, msg + m0, mlen, *v.gs, v.g, v.bar, v.lane);
     int it = 0;
     bool ok = false;
     MaskStream ms{0, 0};
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(256, 4) k_sign_keyed(int n, int n_keys, const 
     else
         sign_zero<LEVEL, P>(tsig, v.g, v.lane);
     if (v.g == 0 && v.lane == 0) {
-        if (status) status[task] = ok ? 0 : -5;
+        if (status) status[task] = ok ? DIL_OK : DIL_EITER;
         if (iters) iters[task] = it;
     }
 }
@@ -79,12 +80,13 @@ __global__ void __launch_bounds__(256, 4) k_verify_keyed(int n, int n_keys, cons
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     const int key = key_idx[task];
-    if (key < 0 || key >= n_keys) {   // unknown key: reject
+    uint64_t m0;
+    size_t mlen;
+    if (key < 0 || key >= n_keys || !message_of(off, task, m0, mlen)) {   // unknown key or bad offsets: reject
         if (v.g == 0 && v.lane == 0) ok[task] = 0;
         return;
     }
-    const uint64_t m0 = off[task], m1 = off[task + 1];
-    int r = verify_task<LEVEL, P, true>(pk + (size_t)key * V::PK, msg + m0, (size_t)(m1 - m0),
+    int r = verify_task<LEVEL, P, true>(pk + (size_t)key * V::PK, msg + m0, mlen,
                                         sig + (size_t)task * V::SIG, scratch + (size_t)task * S::KEYED_VERIFY_POLYS * N,
                                         *v.gs, *v.ws, v.zt, v.izt, v.g, v.bar, v.lane,
                                         keys + (size_t)key * S::KEY_POLYS * N, tr + (size_t)key * 32);

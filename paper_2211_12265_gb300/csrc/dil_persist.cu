@@ -150,9 +150,18 @@ __device__ void own_task(const PersistCtx &pc, int t, const PersistJob &jb, int 
         tk.lock = 0;
         tk.helpers = 0;
     }
-    const uint64_t m0 = jb.off[local], m1 = jb.off[local + 1];
-    sign_prepare<LEVEL, P>(jb.sk + (size_t)local * V::SK, jb.msg + m0, (size_t)(m1 - m0), mine, gs, ws, zt, g, bar,
-                           lane);
+    uint64_t m0;
+    size_t mlen;
+    if (!message_of(jb.off, local, m0, mlen)) {   // decreasing offsets: reject (never published, so no helpers)
+        sign_zero<LEVEL, P>(jb.sig + (size_t)local * V::SIG, g, lane);
+        if (leader) {
+            if (jb.status) jb.status[local] = DIL_EINVAL;
+            if (jb.iters) jb.iters[local] = 0;
+        }
+        group_sync<P>(bar);
+        return;
+    }
+    sign_prepare<LEVEL, P>(jb.sk + (size_t)local * V::SK, jb.msg + m0, mlen, mine, gs, ws, zt, g, bar, lane);
     uint8_t *meta = reinterpret_cast<uint8_t *>(mine + S::SIGN_POLYS * N);
     if (g == 0) {
         meta[lane] = gs.hb[HB_MU + lane];

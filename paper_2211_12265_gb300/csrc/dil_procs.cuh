@@ -134,6 +134,16 @@ __device__ __forceinline__ void pack_seq(uint8_t *dst_poly, const int32_t v[8], 
     pack8<BITS>(dst_poly + BITS * lane, u);
 }
 
+// Task t's message from the n + 1 byte offsets: start m0 and length.  False
+// when the offsets decrease (invalid input): the caller rejects the task
+// instead of reading out of bounds.
+__device__ __forceinline__ bool message_of(const uint64_t *off, int t, uint64_t &m0, size_t &len) {
+    m0 = off[t];
+    const uint64_t m1 = off[t + 1];
+    len = (size_t)(m1 - m0);
+    return m1 >= m0;
+}
+
 // Per-task scratch layout (in polynomials of 256 int32).  Sign's area is a
 // precomputation part (A^, s^1, s^2, t^0: read-only once prepared, shareable
 // between workers) followed by a per-repetition part (y, y^, w, z: private to

@@ -15,9 +15,17 @@ __global__ void __launch_bounds__(256, 4) k_sign(int n, const uint8_t *__restric
     if (task >= n) return;
     using V = Lv<LEVEL>;
     int32_t *scr = scratch + (size_t)task * Scratch<LEVEL>::SIGN_POLYS * N;
-    const uint64_t m0 = off[task], m1 = off[task + 1];
-    sign_prepare<LEVEL, P>(sk + (size_t)task * V::SK, msg + m0, (size_t)(m1 - m0), scr, *v.gs, *v.ws, v.zt, v.g,
-                           v.bar, v.lane);
+    uint64_t m0;
+    size_t mlen;
+    if (!message_of(off, task, m0, mlen)) {   // decreasing offsets: reject the task
+        sign_zero<LEVEL, P>(sig + (size_t)task * V::SIG, v.g, v.lane);
+        if (v.g == 0 && v.lane == 0) {
+            if (status) status[task] = DIL_EINVAL;
+            if (iters) iters[task] = 0;
+        }
+        return;
+    }
+    sign_prepare<LEVEL, P>(sk + (size_t)task * V::SK, msg + m0, mlen, scr, *v.gs, *v.ws, v.zt, v.g, v.bar, v.lane);
     int it = 0;
     bool ok = false;
     MaskStream ms{0, 0};
@@ -33,7 +41,7 @@ __global__ void __launch_bounds__(256, 4) k_sign(int n, const uint8_t *__restric
     else
         sign_zero<LEVEL, P>(tsig, v.g, v.lane);
     if (v.g == 0 && v.lane == 0) {
-        if (status) status[task] = ok ? 0 : -5;
+        if (status) status[task] = ok ? DIL_OK : DIL_EITER;
         if (iters) iters[task] = it;
     }
 }

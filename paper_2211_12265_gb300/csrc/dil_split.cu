@@ -24,7 +24,8 @@ template <int LEVEL, int P>
 __global__ void __launch_bounds__(256, 4) k_split_prepare(int n, const uint8_t *__restrict__ sk,
                                                           const uint8_t *__restrict__ msg,
                                                           const uint64_t *__restrict__ off, int32_t *scratch,
-                                                          SplitState *state) {
+                                                          SplitState *state, uint8_t *sig, int32_t *status,
+                                                          int32_t *iters, int *pending) {
     extern __shared__ __align__(16) uint8_t smem[];
     const CtaView v = cta_setup<P>(smem);
     const int task = blockIdx.x * v.groups + v.group;
@@ -32,8 +33,19 @@ __global__ void __launch_bounds__(256, 4) k_split_prepare(int n, const uint8_t *
     using V = Lv<LEVEL>;
     GroupSmem &gs = *v.gs;
     int32_t *scr = scratch + (size_t)task * Scratch<LEVEL>::SIGN_POLYS * N;
-    sign_prepare<LEVEL, P>(sk + (size_t)task * V::SK, msg + off[task], (size_t)(off[task + 1] - off[task]), scr, gs,
-                           *v.ws, v.zt, v.g, v.bar, v.lane);
+    uint64_t m0;
+    size_t mlen;
+    if (!message_of(off, task, m0, mlen)) {   // decreasing offsets: reject now
+        sign_zero<LEVEL, P>(sig + (size_t)task * V::SIG, v.g, v.lane);
+        if (v.g == 0 && v.lane == 0) {
+            state[task].done = 1;
+            if (status) status[task] = DIL_EINVAL;
+            if (iters) iters[task] = 0;
+            atomicSub(pending, 1);
+        }
+        return;
+    }
+    sign_prepare<LEVEL, P>(sk + (size_t)task * V::SK, msg + m0, mlen, scr, gs, *v.ws, v.zt, v.g, v.bar, v.lane);
     if (v.g == 0) {
         SplitState &st = state[task];
         st.mu[v.lane] = gs.hb[HB_MU + v.lane];
@@ -128,8 +140,9 @@ __global__ void __launch_bounds__(256, 4) k_split_back(int n, int32_t *scratch, 
     return cudaErrorInvalidValue;
 
 static cudaError_t split_prepare(int level, int n, const uint8_t *sk, const uint8_t *msg, const uint64_t *off,
-                                 int32_t *scratch, SplitState *state, int warps, int p, cudaStream_t s) {
-    SPLIT_DISPATCH(k_split_prepare, sk, msg, off, scratch, state)
+                                 int32_t *scratch, SplitState *state, uint8_t *sig, int32_t *status, int32_t *iters,
+                                 int *pending, int warps, int p, cudaStream_t s) {
+    SPLIT_DISPATCH(k_split_prepare, sk, msg, off, scratch, state, sig, status, iters, pending)
 }
 static cudaError_t split_front(int level, int n, int32_t *scratch, SplitState *state, int warps, int p,
                                cudaStream_t s) {
@@ -152,7 +165,7 @@ cudaError_t launch_sign_split(int level, int n, const uint8_t *sk, const uint8_t
     *rounds = 0;
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(pending, &n, sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = split_prepare(level, n, sk, msg, off, scratch, state, warps, p, s);
+    if (e == cudaSuccess) e = split_prepare(level, n, sk, msg, off, scratch, state, sig, status, iters, pending, warps, p, s);
     int left = n;
     while (e == cudaSuccess && left > 0 && *rounds < max_iter) {
         e = split_front(level, n, scratch, state, warps, p, s);

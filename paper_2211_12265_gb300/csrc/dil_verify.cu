@@ -14,8 +14,13 @@ __global__ void __launch_bounds__(256, 4) k_verify(int n, const uint8_t *__restr
     const int task = blockIdx.x * v.groups + v.group;
     if (task >= n) return;
     using V = Lv<LEVEL>;
-    const uint64_t m0 = off[task], m1 = off[task + 1];
-    int r = verify_task<LEVEL, P>(pk + (size_t)task * V::PK, msg + m0, (size_t)(m1 - m0),
+    uint64_t m0;
+    size_t mlen;
+    if (!message_of(off, task, m0, mlen)) {   // decreasing offsets: reject
+        if (v.g == 0 && v.lane == 0) ok[task] = 0;
+        return;
+    }
+    int r = verify_task<LEVEL, P>(pk + (size_t)task * V::PK, msg + m0, mlen,
                                   sig + (size_t)task * V::SIG,
                                   scratch + (size_t)task * Scratch<LEVEL>::VERIFY_POLYS * N, *v.gs, *v.ws, v.zt,
                                   v.izt, v.g, v.bar, v.lane);

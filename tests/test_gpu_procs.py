@@ -284,3 +284,39 @@ def test_split_sign_equals_fused(orc, level):
     for i in (0, n // 2, n - 1):
         _, s, _ = orc.sign(level, skn[i].tobytes(), msg[off[i]:off[i + 1]].tobytes())
         assert s == split[0][i].tobytes()
+
+
+def test_decreasing_offsets_rejected(ctx, orc):
+    """A task whose message offsets decrease is rejected by the kernels (Sign:
+    DIL_EINVAL and a zeroed signature; Verify: 0) without touching the others,
+    in the plain, persistent and split forms; the host forms refuse the call."""
+    import torch
+    from gpu_util import dev, gpu_keygen, gpu_sign, gpu_verify, host
+    from paper_2211_12265_gb300 import dil
+    level = 2
+    seeds = W.seeds(3, 77)
+    pk, sk = gpu_keygen(ctx, level, seeds)
+    msg = np.arange(64, dtype=np.uint8)
+    off = np.array([0, 32, 10, 64], dtype=np.uint64)   # task 1: [32, 10)
+    sig, st, _ = gpu_sign(ctx, level, sk, msg, off)
+    assert st[1] == dil.EINVAL and not sig[1].any()
+    assert st[0] == 0 and st[2] == 0
+    for i, (a, b) in ((0, (0, 32)), (2, (10, 64))):
+        _, s, _ = orc.sign(level, sk[i].tobytes(), msg[a:b].tobytes())
+        assert s == sig[i].tobytes()
+    ok = gpu_verify(ctx, level, pk, msg, off, sig)
+    assert ok[0] == 1 and ok[1] == 0 and ok[2] == 1
+    # persistent and split forms
+    dsk, dmsg, doff = dev(sk), dev(msg), dev(off)
+    psig = torch.full((3, sig.shape[1]), 7, dtype=torch.uint8, device="cuda")
+    pst = torch.full((3,), 9, dtype=torch.int32, device="cuda")
+    dil.dil_sign_persistent(ctx.handle, [dil.sign_job(level, 3, dsk, dmsg, doff, psig, pst)])
+    assert dil.dil_persistent_status(ctx.handle) == dil.OK
+    assert np.array_equal(host(psig), sig) and np.array_equal(host(pst), st)
+    ssig = torch.full_like(psig, 5)
+    sst = torch.full_like(pst, 9)
+    dil.dil_test_sign_split(ctx.handle, level, 3, dsk, dmsg, doff, ssig, sst)
+    assert np.array_equal(host(ssig), sig) and np.array_equal(host(sst), st)
+    # host forms validate on the host
+    with pytest.raises(dil.DilError):
+        dil.dil_sign_host(ctx.handle, level, 3, sk, msg, off, np.zeros_like(sig), np.zeros(3, np.int32))
