@@ -380,6 +380,8 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                       "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),
                       "sign_ms": sign_mean_ms, "verify_ms": float(np.mean(ver_ms)),
                       "mean_sign_repetitions": float(iters.mean()),
+                      "sign_repetitions_histogram": {str(k): int((iters == k).sum()) for k in range(1, 16)} |
+                                                    {">15": int((iters > 15).sum())},
                       "wall_s_timed_region": wall},
         "e2e": {"value": ranks.world * n_ops / (e2e_ms * 1e-3), "unit": "ops/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
@@ -395,6 +397,9 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                                    f"{SM_MAX_MHZ:.0f} MHz max SM clock",
                      "shfl_thread_ops_per_sm_clk": shfl_rate},
         "clocks": clocks,
+        "tuning": {"plain": table.get("plain", {}).get(str(level)),
+                   "persistent": table.get("persistent", {}).get(str(level)),
+                   "source": "paper_2211_12265_gb300/tuning_gb300.json (autotune.py)"},
         "paper_context_a100": PAPER_A100[level],
     }
     ctx.close()

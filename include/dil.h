@@ -48,7 +48,8 @@ typedef enum {
     DIL_ENOMEM = -2,   /* workspace does not fit the budget or the device */
     DIL_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
     DIL_ETIMEOUT = -4, /* a bounded device-side wait ran out (persistent kernels) */
-    DIL_EITER = -5     /* per task: the Sign loop hit its repetition cap */
+    DIL_EITER = -5,    /* per task: the Sign loop hit its repetition cap */
+    DIL_ECANCELED = -6 /* persistent Sign: the host canceled the launch */
 } dil_status;
 
 typedef struct dil_ctx dil_ctx;
@@ -132,7 +133,8 @@ typedef struct {
     const uint8_t *msg;      /* concatenated messages (device, nullable if all empty) */
     const uint64_t *msg_off; /* n + 1 offsets (device) */
     uint8_t *sig;            /* n x SIG (device) */
-    int32_t *task_status;    /* n (device, nullable): DIL_OK or DIL_EITER */
+    int32_t *task_status;    /* n (device, nullable): DIL_OK, DIL_EITER, DIL_EINVAL
+                                (decreasing offsets) or DIL_ECANCELED */
     int32_t *iterations;     /* n (device, nullable): loop repetitions */
 } dil_sign_job;
 
@@ -152,9 +154,23 @@ int dil_sign_persistent(dil_ctx *ctx, int njobs, const dil_sign_job *jobs, void 
 int dil_set_persistent_tuning(dil_ctx *ctx, int warps_per_cta, int warps_per_task, int ctas_per_sm, int chunk,
                               int speculation);
 
-/* Synchronises `stream` and returns DIL_OK, or DIL_ETIMEOUT when a bounded
- * device-side wait of the last persistent launch on this context ran out. */
+/* Synchronises `stream` and returns DIL_OK, DIL_ETIMEOUT when a bounded
+ * device-side wait of the last persistent launch on this context ran out, or
+ * DIL_ECANCELED when that launch was canceled. */
 int dil_persistent_status(dil_ctx *ctx, void *stream);
+
+/* Cancels the persistent launch of this context that is running: sets its
+ * queue's cancel word through a copy on a stream of its own (the launch keeps
+ * the SMs, so no kernel is involved) and returns once the word is written.
+ * The launch then claims no more repetitions: tasks that already hold an
+ * accepting repetition finish as DIL_OK with their normal signature, every
+ * other task ends with status DIL_ECANCELED, 0 iterations and an all-zero
+ * signature, and the grid exits.  A launch that has not started yet resets
+ * the word when it starts, so the cancel applies to it only if it arrives
+ * after that; a cancel after the launch has finished only changes what
+ * dil_persistent_status reports for it.  The context stays usable.  Thread
+ * safe with respect to the caller's stream (the call does not touch it). */
+int dil_persistent_cancel(dil_ctx *ctx);
 
 /* ----------------------------------------------------------------------------
  * Resident keys (for serving many messages per key): a key store keeps, per

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dil.h"
 #include "dil_launch.h"
 
@@ -27,6 +29,7 @@ struct dil_ctx {
     size_t pws_bytes = 0;
     dil::PersistTuning ptune;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cancel_stream = nullptr;   // carries the cancel word's copy
     cudaGraphExec_t gexec = nullptr;
     dil::PersistJobs gjobs{};
     dil::PersistTuning gtune;
@@ -41,6 +44,15 @@ struct dil_ctx {
 namespace {
 
 constexpr size_t POLY_BYTES = 256 * sizeof(int32_t);
+
+// NVTX range over one API call (a no-op unless a profiler is attached), so
+// traces show which entry point issued which launches.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 bool level_ok(int level) { return level == 2 || level == 3 || level == 5; }
 int lidx(int level) { return level == 2 ? 0 : level == 3 ? 1 : 2; }
@@ -146,6 +158,7 @@ int dil_ctx_destroy(dil_ctx *c) {
         if (c->pws) cudaFree(c->pws);
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        if (c->cancel_stream) cudaStreamDestroy(c->cancel_stream);
         for (cudaStream_t a : c->aux)
             if (a) cudaStreamDestroy(a);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -176,6 +189,7 @@ int dil_set_max_iter(dil_ctx *c, int max_iter) {
 }
 
 int dil_keygen(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk, void *stream) {
+    TraceRange trace("dil_keygen");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!seeds || !pk || !sk || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -198,6 +212,7 @@ int dil_keygen(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *p
 
 int dil_sign_ex(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
                 uint8_t *sig, int32_t *task_status, int32_t *iterations, void *stream) {
+    TraceRange trace("dil_sign_ex");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!sk || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -230,6 +245,7 @@ int dil_sign(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *
 
 int dil_verify(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg, const uint64_t *msg_off,
                const uint8_t *sig, uint8_t *ok, void *stream) {
+    TraceRange trace("dil_verify");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!pk || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -276,6 +292,7 @@ bool same_tune(const dil::PersistTuning &a, const dil::PersistTuning &b) {
 }  // namespace
 
 int dil_sign_persistent(dil_ctx *c, int njobs, const dil_sign_job *jobs, void *stream) {
+    TraceRange trace("dil_sign_persistent");
     if (!c || njobs < 1 || njobs > dil::PERSIST_MAX_JOBS || !jobs) return DIL_EINVAL;
     dil::PersistJobs J;
     memset(&J, 0, sizeof(J));
@@ -360,6 +377,17 @@ int dil_persistent_status(dil_ctx *c, void *stream) {
     return dil::persist_error(c->pws);
 }
 
+int dil_persistent_cancel(dil_ctx *c) {
+    TraceRange trace("dil_persistent_cancel");
+    if (!c) return DIL_EINVAL;
+    DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->pws) return DIL_OK;
+    if (!c->cancel_stream && cudaStreamCreateWithFlags(&c->cancel_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return DIL_ECUDA;
+    return dil::persist_cancel(c->pws, c->cancel_stream) == cudaSuccess ? DIL_OK : DIL_ECUDA;
+}
+
 // ---------------------------------------------------------------- key stores
 }  // extern "C"
 
@@ -367,6 +395,7 @@ extern "C" {
 
 int dil_keystore_create(dil_ctx *c, int level, size_t n_keys, const uint8_t *pk, const uint8_t *sk,
                         dil_keystore **out, void *stream) {
+    TraceRange trace("dil_keystore_create");
     if (!c || !out || !level_ok(level) || n_keys == 0 || !pk || n_keys > (size_t)INT32_MAX) return DIL_EINVAL;
     *out = nullptr;
     size_t pkb, skb, sigb;
@@ -414,6 +443,7 @@ int dil_keystore_destroy(dil_keystore *ks) {
 
 int dil_sign_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
                    const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream) {
+    TraceRange trace("dil_sign_keyed");
     if (!c || !ks || !ks->sk || ks->device != c->device) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!key_idx || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -443,6 +473,7 @@ int dil_sign_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *
 
 int dil_verify_keyed(dil_ctx *c, const dil_keystore *ks, size_t n, const int32_t *key_idx, const uint8_t *msg,
                      const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream) {
+    TraceRange trace("dil_verify_keyed");
     if (!c || !ks || ks->device != c->device) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!key_idx || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -570,6 +601,7 @@ extern "C" {
 
 int dil_keygen_host(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8_t *pk, uint8_t *sk,
                     void *stream) {
+    TraceRange trace("dil_keygen_host");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!seeds || !pk || !sk || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -597,6 +629,7 @@ int dil_keygen_host(dil_ctx *c, int level, size_t n, const uint8_t *seeds, uint8
 
 int dil_sign_host(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
                   uint8_t *sig, int32_t *task_status, void *stream) {
+    TraceRange trace("dil_sign_host");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!sk || !msg_off || !sig || n > (size_t)INT32_MAX) return DIL_EINVAL;
@@ -636,6 +669,7 @@ int dil_sign_host(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint
 
 int dil_verify_host(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
                     const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream) {
+    TraceRange trace("dil_verify_host");
     if (!c || !level_ok(level)) return DIL_EINVAL;
     if (n == 0) return DIL_OK;
     if (!pk || !msg_off || !sig || !ok || n > (size_t)INT32_MAX) return DIL_EINVAL;

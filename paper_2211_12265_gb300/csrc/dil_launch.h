@@ -94,7 +94,8 @@ struct PersistTask {
 struct PersistQueue {
     int next_task;
     int error;        // DIL_ETIMEOUT when a bounded wait ran out
-    int pad[30];
+    int cancel;       // set by the host (dil_persistent_cancel) while the launch runs
+    int pad[29];
 };
 struct PersistTuning {
     int warps = 8;        // warps per CTA
@@ -110,6 +111,7 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
                                 int device, cudaStream_t s);
 // Reads the device error word of the last launch on ws (synchronous).
 int persist_error(void *ws);
+cudaError_t persist_cancel(void *ws, cudaStream_t s);
 // Runs the scheduler's bounded wait on a flag holding flag_value (synchronous).
 cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host);
 

@@ -20,6 +20,7 @@
 // DIL_ETIMEOUT in the queue's error word and continues.  The holders of these
 // waits never wait on anything themselves, so the limit is a safety net only.
 #include <climits>
+#include <cstddef>
 
 #include "../../include/dil.h"
 #include "dil_kern.cuh"
@@ -121,7 +122,8 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
         if (leader) {
             const int r = atomicAdd(&tk.next_r, 1);
             const int best = atomicOr(&tk.best_r, 0);
-            gs.claim2 = (r < cap && r < best) ? r : -1;
+            const int canceled = ld_l2(&pc.q->cancel);
+            gs.claim2 = (!canceled && r < cap && r < best) ? r : -1;
         }
         group_sync<P>(bar);
         const int r = *(volatile int *)&gs.claim2;
@@ -134,7 +136,19 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
     }
 }
 
-// Owns task t: prepare, publish, repeat, release, and report a capped task.
+// A task left unsigned because the host canceled the launch: zeroed
+// signature, status DIL_ECANCELED, 0 repetitions.
+template <int LEVEL, int P>
+__device__ void mark_canceled(const PersistJob &jb, int local, int g, int lane) {
+    sign_zero<LEVEL, P>(jb.sig + (size_t)local * Lv<LEVEL>::SIG, g, lane);
+    if (g == 0 && lane == 0) {
+        if (jb.status) jb.status[local] = DIL_ECANCELED;
+        if (jb.iters) jb.iters[local] = 0;
+    }
+}
+
+// Owns task t: prepare, publish, repeat, release, and report a capped or
+// canceled task.
 template <int LEVEL, int P>
 __device__ void own_task(const PersistCtx &pc, int t, const PersistJob &jb, int local, int slot, int32_t *mine,
                          GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt, int g, int bar,
@@ -178,17 +192,20 @@ __device__ void own_task(const PersistCtx &pc, int t, const PersistJob &jb, int 
         atomicExch(&pc.slot_task[slot], -1);
         __threadfence();
         if (!wait_until_zero(&tk.helpers, PERSIST_SPIN_LIMIT)) atomicExch(&pc.q->error, DIL_ETIMEOUT);
-        gs.claim2 = (atomicOr(&tk.best_r, 0) == INT_MAX) ? 1 : 0;
+        // no accepting repetition: the cap was reached, or the host canceled the launch
+        gs.claim2 = (atomicOr(&tk.best_r, 0) != INT_MAX) ? 0 : ld_l2(&pc.q->cancel) ? 2 : 1;
     }
     group_sync<P>(bar);
-    const int capped = *(volatile int *)&gs.claim2;
+    const int unsigned_task = *(volatile int *)&gs.claim2;
     group_sync<P>(bar);
-    if (capped) {
+    if (unsigned_task == 1) {
         sign_zero<LEVEL, P>(jb.sig + (size_t)local * V::SIG, g, lane);
         if (leader) {
             if (jb.status) jb.status[local] = DIL_EITER;
             if (jb.iters) jb.iters[local] = iter_cap<LEVEL>(pc.max_iter_override);
         }
+    } else if (unsigned_task == 2) {
+        mark_canceled<LEVEL, P>(jb, local, g, lane);
     }
 }
 
@@ -224,17 +241,30 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
     PersistCtx pc{q, tasks, slot_task, scratch, slot_polys, (int)gridDim.x * v.groups, max_iter_override, spec};
     const int slot = blockIdx.x * v.groups + v.group;
     int32_t *mine = scratch + (size_t)slot * slot_polys * N;
-    // fresh tasks
+    // fresh tasks (after a host cancel, the rest of the queue is only marked)
+    bool canceled = false;
     for (;;) {
-        if (leader) gs.claim = atomicAdd(&q->next_task, chunk);
+        if (leader) {
+            gs.claim = atomicAdd(&q->next_task, chunk);
+            gs.claim2 = ld_l2(&q->cancel);
+        }
         group_sync<P>(bar);
         const int c0 = *(volatile int *)&gs.claim;
+        canceled = *(volatile int *)&gs.claim2 != 0;
         group_sync<P>(bar);
         if (c0 >= J.total) break;
         const int c1 = min(c0 + chunk, J.total);
         for (int t = c0; t < c1; ++t) {
             int local;
             const PersistJob &jb = job_of(J, t, local);
+            if (canceled) {
+                switch (jb.level) {
+                    case 2: mark_canceled<2, P>(jb, local, g, lane); break;
+                    case 3: mark_canceled<3, P>(jb, local, g, lane); break;
+                    default: mark_canceled<5, P>(jb, local, g, lane); break;
+                }
+                continue;
+            }
             switch (jb.level) {
                 case 2: own_task<2, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
                 case 3: own_task<3, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
@@ -242,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
             }
         }
     }
-    if (spec <= 0) return;
+    if (spec <= 0 || canceled || ld_l2(&q->cancel)) return;
     // speculative help on unfinished tasks (predicted nonces)
     int start = (int)(((unsigned)slot * 2654435761u) % (unsigned)pc.slots);
     for (int round = 0; round < 4096; ++round) {
@@ -413,7 +443,17 @@ cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host) {
 int persist_error(void *ws) {
     PersistQueue h;
     if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DIL_ECUDA;
-    return h.error ? DIL_ETIMEOUT : DIL_OK;
+    return h.error ? DIL_ETIMEOUT : h.cancel ? DIL_ECANCELED : DIL_OK;
+}
+
+// Sets the queue's cancel word of a running launch through a copy engine on
+// stream s (a kernel could not start while the persistent grid holds the SMs).
+cudaError_t persist_cancel(void *ws, cudaStream_t s) {
+    static const int one = 1;
+    cudaError_t e = cudaMemcpyAsync(static_cast<char *>(ws) + offsetof(PersistQueue, cancel), &one, sizeof(int),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
 }
 
 }  // namespace dil

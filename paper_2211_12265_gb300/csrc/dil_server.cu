@@ -31,6 +31,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dil.h"
 #include "dil_launch.h"
 
@@ -202,6 +204,7 @@ bool dispatch(dil_server *sv, Slot &s) {
         if (!sv->pending.empty()) sv->cv_work.notify_one();   // another slot may take the rest
     }
     if (s.reqs.empty()) return false;
+    nvtxRangePushA("dil_server_batch");   // host side of one batch: staging and launches
     // group by (op, level), stable within a group
     std::stable_sort(s.reqs.begin(), s.reqs.end(), [](const Req *a, const Req *b) {
         return a->op != b->op ? a->op < b->op : a->level < b->level;
@@ -266,6 +269,7 @@ bool dispatch(dil_server *sv, Slot &s) {
     check(cudaEventRecord(s.done, st));
     s.failed = err != cudaSuccess;
     s.busy = true;
+    nvtxRangePop();
     sv->batches++;
     sv->launches += s.groups.size();
     sv->batched_reqs += n;

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EITER = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EITER, ECANCELED = 0, -1, -2, -3, -4, -5, -6
 SIZES = {2: (1312, 2528, 2420), 3: (1952, 4000, 3293), 5: (2592, 4864, 4595)}
 PARAMS = {2: dict(k=4, l=4), 3: dict(k=6, l=5), 5: dict(k=8, l=7)}
 
@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
                 "dil_persistent_status": [P, P],
+                "dil_persistent_cancel": [P],
                 "dil_keystore_create": [P, I, S, P, P, P, P],
                 "dil_keystore_destroy": [P],
                 "dil_sign_keyed": [P, P, S, P, P, P, P, P, P],
@@ -299,6 +300,10 @@ def dil_set_persistent_tuning(ctx, warps_per_cta=8, warps_per_task=2, ctas_per_s
 
 def dil_persistent_status(ctx, stream=None) -> int:
     return load().dil_persistent_status(ctx, _stream(stream))
+
+
+def dil_persistent_cancel(ctx) -> int:
+    return load().dil_persistent_cancel(ctx)
 
 
 def dil_keystore_create(ctx, level, n_keys, pk, sk=None, stream=None) -> int:

@@ -110,3 +110,36 @@ def test_repetition_cap_with_speculation(torch_cuda, orc):
         (got,) = _persistent(torch_cuda, ctx, [j])
     assert np.array_equal(got[1], ost) and np.array_equal(got[0], osig) and np.array_equal(got[2], oit)
     assert (ost == -5).any() and (ost == 0).any()
+
+
+def test_cancel_running_launch(torch_cuda):
+    """A host cancel during a long launch: every task ends either signed
+    exactly as the plain form signs it, or DIL_ECANCELED with a zero
+    signature; the next launch on the same context runs to completion."""
+    import time
+    from paper_2211_12265_gb300 import dil
+    torch = torch_cuda
+    n = 400_000
+    j = _job_inputs(torch, 2, n, 38)
+    with dil.Context(0) as ctx:
+        assert dil.dil_persistent_cancel(ctx.handle) == dil.OK   # nothing launched yet: no effect
+        sig = torch.full((n, dil.SIZES[2][2]), 0x5A, dtype=torch.uint8, device="cuda")
+        st = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+        it = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+        desc = dil.sign_job(2, n, j["sk"], j["msg"], j["off"], sig, st, it)
+        dil.dil_sign_persistent(ctx.handle, [desc])
+        time.sleep(0.02)
+        assert dil.dil_persistent_cancel(ctx.handle) == dil.OK
+        assert dil.dil_persistent_status(ctx.handle) == dil.ECANCELED
+        s, g, i = st.cpu().numpy(), sig.cpu().numpy(), it.cpu().numpy()
+        ok, canceled = s == dil.OK, s == dil.ECANCELED
+        assert (ok | canceled).all()
+        assert ok.sum() > 0 and canceled.sum() > 0
+        assert not g[canceled].any() and not i[canceled].any()
+        rsig, rst, rit = _plain(torch, j)
+        assert np.array_equal(g[ok], rsig[ok]) and np.array_equal(i[ok], rit[ok])
+        # the context is reusable and the next launch starts with the word cleared
+        small = _job_inputs(torch, 2, 500, 39)
+        (got,) = _persistent(torch, ctx, [small])
+    for a, b in zip(got, _plain(torch, small)):
+        assert np.array_equal(a, b)
