@@ -109,7 +109,7 @@ int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8
  * dil_sign without a context; runs on the current device with the default
  * repetition cap.  Scratch is a 64 MiB array inside the library's device image
  * (held by every GPU that loads the library until exit), so n may not exceed
- * 1337 / 897 / 579 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
+ * 1110 / 789 / 532 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
  * The first call on a device looks up the array's address (cudaGetSymbolAddress)
  * and should come before any stream capture.  All calls share the array: calls
  * that overlap on the GPU race and must be serialised.  Nothing in it needs
@@ -292,6 +292,13 @@ int dil_verify_host(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const 
  * strings (in, in_off as for messages) -> outlen bytes each (out: n x outlen). */
 int dil_test_shake(dil_ctx *ctx, int kind, size_t n, const uint8_t *in, const uint64_t *in_off,
                    uint8_t *out, size_t outlen, void *stream);
+/* Keccak-f[1600] (FIPS 202; section 3.3 of arXiv 2211.12265 for the warp
+ * form) of n states, each 25 little-endian 64-bit lanes, lane x + 5y at
+ * index x + 5y (in, out: n x 25 uint64, device).  form selects the
+ * permutation code the kernels use: 1 = one state on 25 lanes, 2 = two
+ * interleaved states, 6 = six states in the skewed row layout, 16 = sixteen
+ * states on two threads each.  DIL_EINVAL for another form. */
+int dil_test_keccak_f(dil_ctx *ctx, int form, size_t n, const uint64_t *in, uint64_t *out, void *stream);
 /* Forward (inverse = 0) or inverse (inverse = 1) NTT of n polynomials of 256
  * int32 coefficients (any representatives with |a| < q); outputs in [0, q). */
 int dil_test_ntt(dil_ctx *ctx, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream);
@@ -339,7 +346,8 @@ int dil_test_sign_split(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, co
 /* Test only: throughput of the Keccak-f[1600] forms the kernels use (section
  * 3.3 of arXiv 2211.12265 describes the first), in SM clocks per state per
  * round, 32 warps per SM, every state independent.  form: 1 = one state on 25
- * lanes, 2 = two interleaved states, 6 = six states in the skewed row layout.
+ * lanes, 2 = two interleaved states, 6 = six states in the skewed row layout,
+ * 16 = sixteen states on two threads each.
  * Synchronous; allocates and frees a small buffer.  DIL_EINVAL for another
  * form or a NULL output. */
 int dil_test_keccak_rate(dil_ctx *ctx, int form, double *sm_clocks_per_state_round);

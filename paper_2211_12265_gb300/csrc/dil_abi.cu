@@ -720,6 +720,14 @@ int dil_test_shake(dil_ctx *c, int kind, size_t n, const uint8_t *in, const uint
     return status_of(dil::launch_test_shake(kind, (int)n, in, in_off, out, (int)outlen, (cudaStream_t)stream));
 }
 
+int dil_test_keccak_f(dil_ctx *c, int form, size_t n, const uint64_t *in, uint64_t *out, void *stream) {
+    TEST_PROLOGUE(c)
+    if ((form != 1 && form != 2 && form != 6 && form != 16) || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!in || !out) return DIL_EINVAL;
+    return status_of(dil::launch_test_keccak_f(form, (int)n, in, out, (cudaStream_t)stream));
+}
+
 int dil_test_ntt(dil_ctx *c, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream) {
     TEST_PROLOGUE(c)
     if (n > (size_t)INT32_MAX || (n && (!in || !out))) return DIL_EINVAL;
@@ -806,7 +814,7 @@ int dil_test_sign_split(dil_ctx *c, int level, size_t n, const uint8_t *sk, cons
 
 int dil_test_keccak_rate(dil_ctx *c, int form, double *sm_clocks_per_state_round) {
     TEST_PROLOGUE(c)
-    if ((form != 1 && form != 2 && form != 6) || !sm_clocks_per_state_round) return DIL_EINVAL;
+    if ((form != 1 && form != 2 && form != 6 && form != 16) || !sm_clocks_per_state_round) return DIL_EINVAL;
     return status_of(dil::measure_keccak_rate(form, sm_clocks_per_state_round));
 }
 

@@ -8,6 +8,7 @@
 
 #include <vector>
 
+#include "dil_keccak16.cuh"
 #include "dil_keccak6.cuh"
 #include "dil_launch.h"
 
@@ -87,16 +88,17 @@ constexpr int KPROBE_WARPS = 8;
 constexpr int KPROBE_CTAS_PER_SM = 4;
 
 // Every warp permutes its FORM states (1: 25-lane form, 2: two interleaved
-// states, 6: six-state row form) KPROBE_PERMS times.
+// states, 6: six-state row form, 16: two-thread-per-state form)
+// KPROBE_PERMS times.
 template <int FORM>
 __global__ void __launch_bounds__(KPROBE_WARPS * 32, KPROBE_CTAS_PER_SM) k_keccak_probe(uint32_t *out,
                                                                                        long long *cyc) {
-    __shared__ __align__(16) uint32_t sm[KPROBE_WARPS][640];   // 300 state words + 320 exchange words
+    __shared__ __align__(16) uint32_t sm[KPROBE_WARPS][K16_WORDS];   // six states + exchange, or sixteen states
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *kst = sm[warp], *kpi = kst + K6_STATES * K6_WORDS;
     uint32_t lo = lane * 0x9E3779B9u + blockIdx.x, hi = lo ^ 0x5BD1E995u, lo1 = lo + 1, hi1 = hi + 1;
-    if (FORM == 6) {
-        for (int w = lane; w < K6_STATES * K6_WORDS; w += 32) kst[w] = w * 2654435761u + blockIdx.x;
+    if (FORM == 6 || FORM == 16) {
+        for (int w = lane; w < K16_WORDS; w += 32) kst[w] = w * 2654435761u + blockIdx.x;
     }
     __syncthreads();
     const long long t0 = clock64();
@@ -104,11 +106,12 @@ __global__ void __launch_bounds__(KPROBE_WARPS * 32, KPROBE_CTAS_PER_SM) k_kecca
         if (FORM == 1) keccak_f(lo, hi);
         if (FORM == 2) keccak_f2(lo, hi, lo1, hi1);
         if (FORM == 6) keccak6_permute(kst, kpi);
+        if (FORM == 16) keccak16_permute(kst);
     }
     __syncthreads();
     const long long t1 = clock64();
     if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
-    out[blockIdx.x * blockDim.x + threadIdx.x] = lo ^ hi ^ lo1 ^ hi1 ^ (FORM == 6 ? kst[lane] : 0u);
+    out[blockIdx.x * blockDim.x + threadIdx.x] = lo ^ hi ^ lo1 ^ hi1 ^ (FORM >= 6 ? kst[lane] : 0u);
 }
 
 cudaError_t measure_keccak_rate(int form, double *clk_per_state_round) {
@@ -129,6 +132,7 @@ cudaError_t measure_keccak_rate(int form, double *clk_per_state_round) {
         if (form == 1) k_keccak_probe<1><<<blocks, threads>>>(out, cyc);
         if (form == 2) k_keccak_probe<2><<<blocks, threads>>>(out, cyc);
         if (form == 6) k_keccak_probe<6><<<blocks, threads>>>(out, cyc);
+        if (form == 16) k_keccak_probe<16><<<blocks, threads>>>(out, cyc);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }

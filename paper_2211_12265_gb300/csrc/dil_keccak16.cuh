@@ -1,0 +1,127 @@
+// Sixteen Keccak-f[1600] instances per warp, two threads per instance (bulk
+// sponges of the samplers when a warp has seven or more sponges to run).
+//
+// Lane 2s + p holds half p of every lane of instance s: the low 32-bit word
+// of each 64-bit state lane (p = 0) or the high word (p = 1), i.e. 25
+// registers.  Everything in a round but the 64-bit rotations is
+// word-local: theta's column parities, chi along the rows and pi (a renaming
+// of registers) need no exchange at all.  A 64-bit rotation by r needs both
+// words of the lane: each thread fetches its partner's word with one
+// shuffle and keeps its own half of the rotated lane with one funnel shift,
+// the same expression on both threads (mine m, partner v: r < 32 gives
+// fshl(v, m, r), r >= 32 gives fshl(m, v, r - 32)).  Per round that is 24
+// shuffles for rho and 5 for theta's rotation by one, about 125 instructions
+// per thread for 16 instances (about 8 warp instructions per instance-round,
+// against about 15 for the six-state row form and 66 for the 25-lane form),
+// and no shared-memory traffic inside the permutation.
+//
+// Between permutations the states live in shared memory (`kst`, 800 words):
+// word i (lane i = x + 5y of the state) of thread `lane` at 32 i + lane, so
+// every thread reaches its words without bank conflicts, and byte-stream
+// word w (4 bytes) of instance s sits at 32 (w >> 1) + 2 s + (w & 1).
+#pragma once
+#include "dil_keccak.cuh"
+#include "dil_ntt.cuh"
+
+namespace dil {
+
+constexpr int K16_STATES = 16;
+constexpr int K16_WORDS = 25 * 32;   // shared words of the sixteen states
+
+// Shared-memory word of byte-stream word w of instance s.
+__device__ __forceinline__ int k16_word(int s, int w) { return 32 * (w >> 1) + 2 * s + (w & 1); }
+
+namespace detail {
+// FIPS 202 rho offset of lane (x, y).
+__host__ __device__ constexpr int k16_rho(int x, int y) {
+    return (y == 0)   ? (x == 0 ? 0 : x == 1 ? 1 : x == 2 ? 62 : x == 3 ? 28 : 27)
+           : (y == 1) ? (x == 0 ? 36 : x == 1 ? 44 : x == 2 ? 6 : x == 3 ? 55 : 20)
+           : (y == 2) ? (x == 0 ? 3 : x == 1 ? 10 : x == 2 ? 43 : x == 3 ? 25 : 39)
+           : (y == 3) ? (x == 0 ? 41 : x == 1 ? 45 : x == 2 ? 15 : x == 3 ? 21 : 8)
+                      : (x == 0 ? 18 : x == 1 ? 2 : x == 2 ? 61 : x == 3 ? 56 : 14);
+}
+}  // namespace detail
+
+// This thread's half of rotl64(lane, R) given its word m of the lane.
+template <int R>
+__device__ __forceinline__ uint32_t k16_rot(uint32_t m) {
+    if constexpr (R == 0) {
+        return m;
+    } else {
+        const uint32_t v = __shfl_xor_sync(FULL, m, 1);
+        if constexpr (R < 32)
+            return __funnelshift_l(v, m, R);
+        else
+            return __funnelshift_l(m, v, R - 32);
+    }
+}
+
+// rho + pi for source lane i = x + 5y: B[y + 5 ((2x + 3y) mod 5)] = rotl(A[i]).
+template <int I>
+__device__ __forceinline__ void k16_rho_pi(uint32_t (&b)[25], const uint32_t (&a)[25]) {
+    constexpr int x = I % 5, y = I / 5;
+    b[y + 5 * ((2 * x + 3 * y) % 5)] = k16_rot<detail::k16_rho(x, y)>(a[I]);
+    if constexpr (I < 24) k16_rho_pi<I + 1>(b, a);
+}
+
+// Permutes the sixteen states at shared address kst (K16_WORDS words).  Called
+// by all 32 lanes of the warp.  Out of line: one copy serves every sampler.
+static __device__ __noinline__ void keccak16_permute_impl(uint32_t kst) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t base = kst + 4 * lane;
+    const bool high = lane & 1;
+    uint32_t a[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[i]) : "r"(base + 128 * i));
+#pragma unroll 1
+    for (int round = 0; round < 24; ++round) {
+        // theta
+        uint32_t c[5], d[5];
+#pragma unroll
+        for (int x = 0; x < 5; ++x) c[x] = a[x] ^ a[x + 5] ^ a[x + 10] ^ a[x + 15] ^ a[x + 20];
+#pragma unroll
+        for (int x = 0; x < 5; ++x) d[x] = k16_rot<1>(c[x]);   // this half of rotl(C[x], 1)
+#pragma unroll
+        for (int i = 0; i < 25; ++i) a[i] ^= c[(i + 4) % 5] ^ d[(i + 1) % 5];
+        // rho + pi
+        uint32_t b[25];
+        k16_rho_pi<0>(b, a);
+        // chi
+#pragma unroll
+        for (int y = 0; y < 5; ++y)
+#pragma unroll
+            for (int x = 0; x < 5; ++x)
+                a[x + 5 * y] = b[x + 5 * y] ^ (~b[(x + 1) % 5 + 5 * y] & b[(x + 2) % 5 + 5 * y]);
+        // iota
+        const uint64_t rc = c_keccak_rc[round];
+        a[0] ^= high ? (uint32_t)(rc >> 32) : (uint32_t)rc;
+    }
+#pragma unroll
+    for (int i = 0; i < 25; ++i) asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + 128 * i), "r"(a[i]) : "memory");
+    __syncwarp();
+}
+
+__device__ __forceinline__ void keccak16_permute(uint32_t *kst) { keccak16_permute_impl(smem_addr(kst)); }
+
+// Initialises the sixteen states with padded one-block seeds: byte-stream
+// words [0, seed_words) from `seed` (shared memory), then the word
+// tail_of(s) (the instance's nonce bytes followed by the SHAKE
+// domain/padding byte 0x1F), and the final padding bit at the last byte of
+// the rate.  Instances >= count get the same seed with tail 0 (their output is
+// never read).
+template <class Tail>
+__device__ __forceinline__ void keccak16_seed(uint32_t *kst, const uint32_t *seed, int seed_words, Tail tail_of,
+                                              int count, int rate, int lane) {
+    const int s = lane >> 1, p = lane & 1;
+    const uint32_t tail = s < count ? tail_of(s) : 0u;
+#pragma unroll 1
+    for (int i = 0; i < 25; ++i) {
+        const int w = 2 * i + p;
+        uint32_t v = w < seed_words ? seed[w] : w == seed_words ? tail : 0u;
+        if (w == rate / 4 - 1) v ^= 0x80000000u;
+        kst[32 * i + lane] = v;
+    }
+    __syncwarp();
+}
+
+}  // namespace dil

@@ -56,8 +56,61 @@ __global__ void k_test_ntt(int n, const int32_t *in, int32_t *out, int inverse) 
     }
 }
 
-// Covers the single, pair and six-sponge forms: polynomial 0 alone, 1-2 as a
-// pair, the rest as one range (six at a time, then the tail).
+// Keccak-f[1600] of `states` states (25 little-endian 64-bit lanes each) in
+// one of the permutation forms; warp `item` permutes states
+// [FORM item, FORM item + FORM).
+template <int FORM>
+__global__ void k_test_keccak_f(int n, int states, const uint64_t *in, uint64_t *out) {
+    PRIM_PROLOGUE
+    const int s0 = item * FORM;
+    if constexpr (FORM == 1 || FORM == 2) {
+        uint32_t lo[2] = {0, 0}, hi[2] = {0, 0};
+#pragma unroll
+        for (int k = 0; k < FORM; ++k) {
+            if (lane < 25 && s0 + k < states) {
+                const uint64_t w = in[(size_t)(s0 + k) * 25 + lane];
+                lo[k] = (uint32_t)w;
+                hi[k] = (uint32_t)(w >> 32);
+            }
+        }
+        if constexpr (FORM == 1)
+            keccak_f(lo[0], hi[0]);
+        else
+            keccak_f2(lo[0], hi[0], lo[1], hi[1]);
+#pragma unroll
+        for (int k = 0; k < FORM; ++k)
+            if (lane < 25 && s0 + k < states) out[(size_t)(s0 + k) * 25 + lane] = ((uint64_t)hi[k] << 32) | lo[k];
+    } else if constexpr (FORM == 6) {
+        for (int w = lane; w < K6_STATES * K6_WORDS; w += 32) {
+            const int g = w / K6_WORDS, i = (w % K6_WORDS) >> 1, h = w & 1;
+            ws.kst[w] = s0 + g < states ? (uint32_t)(in[(size_t)(s0 + g) * 25 + i] >> (32 * h)) : 0u;
+        }
+        __syncwarp();
+        keccak6_permute(ws.kst, ws.kpi());
+        for (int w = lane; w < K6_STATES * 25; w += 32) {
+            const int g = w / 25, i = w % 25;
+            if (s0 + g < states)
+                out[(size_t)(s0 + g) * 25 + i] =
+                    ((uint64_t)ws.kst[K6_WORDS * g + 2 * i + 1] << 32) | ws.kst[K6_WORDS * g + 2 * i];
+        }
+    } else {
+        const int st = lane >> 1, h = lane & 1;
+        for (int i = 0; i < 25; ++i)
+            ws.k16[32 * i + lane] = s0 + st < states ? (uint32_t)(in[(size_t)(s0 + st) * 25 + i] >> (32 * h)) : 0u;
+        __syncwarp();
+        keccak16_permute(ws.k16);
+        for (int w = lane; w < K16_STATES * 25; w += 32) {
+            const int g = w / 25, i = w % 25;
+            if (s0 + g < states)
+                out[(size_t)(s0 + g) * 25 + i] =
+                    ((uint64_t)ws.k16[32 * i + 2 * g + 1] << 32) | ws.k16[32 * i + 2 * g];
+        }
+    }
+}
+
+// Covers the single, pair, six- and sixteen-sponge forms: polynomial 0 alone,
+// 1-2 as a pair, 3-8 as one six-sponge range, the rest as one range (sixteen
+// at a time while at least seven remain, then the tail).
 template <int LEVEL>
 __global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
     PRIM_PROLOGUE
@@ -67,7 +120,8 @@ __global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
     int32_t *o = out + (size_t)item * V::K * V::L * N;
     expand_a_range<LEVEL>(gs.rho, 0, 1, o, ws, lane);
     expand_a_range<LEVEL>(gs.rho, 1, 3, o, ws, lane);
-    expand_a_range<LEVEL>(gs.rho, 3, V::K * V::L, o, ws, lane);
+    expand_a_range<LEVEL>(gs.rho, 3, 9, o, ws, lane);
+    expand_a_range<LEVEL>(gs.rho, 9, V::K * V::L, o, ws, lane);
 }
 
 template <int LEVEL>
@@ -85,9 +139,9 @@ __global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
     }
 }
 
-// Even items: all l polynomials through six-sponge batches (with a pair or
-// single tail where l is not a multiple of six); odd items: single, pair and
-// the rest.
+// Items 0 mod 3: all l polynomials through six-sponge batches (with a pair or
+// single tail where l is not a multiple of six); 1 mod 3: single, pair and
+// the rest; 2 mod 3: one sixteen-sponge batch of l instances.
 template <int LEVEL>
 __global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out) {
     PRIM_PROLOGUE
@@ -97,7 +151,12 @@ __global__ void k_test_expand_mask(int n, const uint8_t *rhop, const int32_t *ka
     int32_t *o = out + (size_t)item * V::L * N;
     int32_t a[8], b[8];
     int j = 0;
-    if (item & 1) {
+    if (item % 3 == 2) {
+        expand_mask_16<V::ZBITS, V::GAMMA1>(
+            gs.rhop, kappa[item], V::L, [&](int s) { return o + s * N; }, ws.k16, ws.k16c, lane);
+        return;
+    }
+    if (item % 3 == 1) {
         expand_mask_poly<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item], a, ws.sq, lane);
         store_l0(o, a, lane);
         expand_mask_pair<V::ZBITS, V::GAMMA1>(gs.rhop, kappa[item] + 1, kappa[item] + 2, a, b, ws.sq, ws.sq2,
@@ -171,6 +230,16 @@ cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t
 }
 cudaError_t launch_test_ntt(int n, const int32_t *in, int32_t *out, int inverse, cudaStream_t s) {
     return launch_prim(k_test_ntt, n, s, in, out, inverse);
+}
+cudaError_t launch_test_keccak_f(int form, int states, const uint64_t *in, uint64_t *out, cudaStream_t s) {
+    const int items = (states + form - 1) / form;
+    switch (form) {
+        case 1: return launch_prim(k_test_keccak_f<1>, items, s, states, in, out);
+        case 2: return launch_prim(k_test_keccak_f<2>, items, s, states, in, out);
+        case 6: return launch_prim(k_test_keccak_f<6>, items, s, states, in, out);
+        case 16: return launch_prim(k_test_keccak_f<16>, items, s, states, in, out);
+    }
+    return cudaErrorInvalidValue;
 }
 cudaError_t launch_test_expand_a(int level, int n, const uint8_t *rho, int32_t *out, cudaStream_t s) {
     BY_LEVEL(k_test_expand_a, rho, out)

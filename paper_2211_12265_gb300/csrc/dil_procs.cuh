@@ -18,21 +18,29 @@
 
 namespace dil {
 
-// Per-warp shared memory.  The six-state sponges (states, field windows) and
-// the one- and two-state ones (sampled polynomials, squeezed blocks) are never
-// live at the same time and share one area; buf doubles as the six-state
-// permutation's pi exchange.
+// Per-warp shared memory.  The sixteen-state sponges, the six-state ones
+// (states, field windows) and the one- and two-state ones (sampled
+// polynomials, squeezed blocks) are never live at the same time and share one
+// area; buf doubles as the six-state permutation's pi exchange.
 struct __align__(16) WarpSmem {
-    int32_t buf[K6_PI_WORDS];      // NTT exchanges / sampled polynomial (padded) / keccak6 pi exchange
     union {
         struct {
-            int32_t buf2[288];     // second sampled polynomial of a pair
-            uint8_t sq[688];       // squeezed SHAKE blocks (5 x 136 + slack)
-            uint8_t sq2[688];      // squeezed blocks of the second sponge of a pair
+            int32_t buf[K6_PI_WORDS];      // NTT exchanges / sampled polynomial (padded) / keccak6 pi exchange
+            union {
+                struct {
+                    int32_t buf2[288];     // second sampled polynomial of a pair
+                    uint8_t sq[688];       // squeezed SHAKE blocks (5 x 136 + slack)
+                    uint8_t sq2[688];      // squeezed blocks of the second sponge of a pair
+                };
+                struct {
+                    uint32_t kst[K6_STATES * K6_WORDS];   // six Keccak states
+                    uint32_t win[K6_STATES * 38];         // ExpandMask field windows
+                };
+            };
         };
         struct {
-            uint32_t kst[K6_STATES * K6_WORDS];   // six Keccak states
-            uint32_t win[K6_STATES * 38];         // ExpandMask field windows
+            uint32_t k16[K16_WORDS];   // sixteen Keccak states
+            uint32_t k16c[32];         // ExpandMask carry: each state's previous last lane
         };
     };
     __device__ uint32_t *kpi() { return reinterpret_cast<uint32_t *>(buf); }
@@ -156,10 +164,11 @@ template <int LEVEL> struct Scratch {
     static constexpr int T0H = S2H + V::K;
     static constexpr int PRE_POLYS = T0H + V::K;
     // offsets inside the per-repetition part; y is a ring of YRING
-    // polynomials indexed by nonce (a worker samples masks six nonces at a
-    // time and keeps the ones the next repetition needs)
+    // polynomials indexed by nonce (a one-warp worker samples masks
+    // MASK_BATCH nonces at a time and keeps the ones later repetitions need)
+    static constexpr int MASK_BATCH = K16_STATES;
     static constexpr int Y = 0;
-    static constexpr int YRING = V::L + K6_STATES - 1;
+    static constexpr int YRING = V::L + MASK_BATCH - 1;
     static constexpr int YH = Y + YRING;
     static constexpr int W = YH + V::L;
     static constexpr int Z = W + V::K;
@@ -178,12 +187,18 @@ template <int LEVEL> struct Scratch {
 template <int M, int P>
 __device__ __forceinline__ int share_lo(int g) { return g * M / P; }
 
-// A^_p (p = i l + j) for p in [lo, hi) into out + p N in index order: six
-// sponges at a time while at least three remain, then a pair or a single.
+// A^_p (p = i l + j) for p in [lo, hi) into out + p N in index order: up to
+// sixteen sponges at a time while at least seven remain, six at a time while
+// at least three remain, then a pair or a single.
 template <int LEVEL>
 __device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out, WarpSmem &ws, int lane) {
     constexpr int L = Lv<LEVEL>::L;
     int p = lo;
+    while (hi - p >= 7) {
+        const int c = min(K16_STATES, hi - p);
+        expand_a_16<L>(rho, p, c, out + p * N, ws.k16, lane);
+        p += c;
+    }
     while (hi - p >= 3) {
         const int c = min(K6_STATES, hi - p);
         expand_a_six<L>(rho, p, c, out + p * N, ws.kst, ws.kpi(), lane);
@@ -219,6 +234,19 @@ __device__ void expand_mask_range(const uint8_t *rhop, int kappa, int lo, int hi
     using V = Lv<LEVEL>;
     int32_t r[8], a[8];
     int j = lo;
+    while (hi - j >= 7) {
+        const int c = min(K16_STATES, hi - j), u0 = kappa + j;
+        expand_mask_16<V::ZBITS, V::GAMMA1>(
+            rhop, u0, c, [&](int s) { return y_slot<LEVEL>(ring, u0 + s); }, ws.k16, ws.k16c, lane);
+        __syncwarp();
+#pragma unroll 1
+        for (int u = j; u < j + c; ++u) {
+            load_l0(r, y_slot<LEVEL>(ring, kappa + u), lane);
+            ntt_fwd(r, ws.buf, zt, lane);
+            store_l2(yh + u * N, r, lane);
+        }
+        j += c;
+    }
     while (hi - j >= 3) {
         const int c = min(K6_STATES, hi - j), u0 = kappa + j;
         expand_mask_six<V::ZBITS, V::GAMMA1>(
@@ -253,9 +281,9 @@ struct MaskStream {
 };
 
 // One-warp form: y for nonces [kappa, kappa + l) from the stream, which
-// samples six consecutive nonces at a time, so the leftovers of one
-// repetition serve the next (a repetition that does not continue the stream
-// restarts it at kappa); y^ into yh.
+// samples MASK_BATCH (sixteen) consecutive nonces at a time, so the leftovers
+// of one repetition serve the next ones (a repetition that does not continue
+// the stream restarts it at kappa); y^ into yh.
 template <int LEVEL>
 __device__ void mask_stream(const uint8_t *rhop, int kappa, MaskStream &ms, int32_t *ring, int32_t *yh,
                             WarpSmem &ws, const int32_t *zt, int lane) {
@@ -264,10 +292,9 @@ __device__ void mask_stream(const uint8_t *rhop, int kappa, MaskStream &ms, int3
     ms.lo = kappa;
     while (ms.hi < kappa + V::L) {   // live nonces stay within [kappa, kappa + YRING)
         const int u0 = ms.hi;
-        expand_mask_six<V::ZBITS, V::GAMMA1>(
-            rhop, u0, K6_STATES, [&](int g) { return y_slot<LEVEL>(ring, u0 + g); }, ws.kst, ws.kpi(), ws.win,
-            lane);
-        ms.hi += K6_STATES;
+        expand_mask_16<V::ZBITS, V::GAMMA1>(
+            rhop, u0, K16_STATES, [&](int s) { return y_slot<LEVEL>(ring, u0 + s); }, ws.k16, ws.k16c, lane);
+        ms.hi += Scratch<LEVEL>::MASK_BATCH;
     }
     __syncwarp();
     int32_t r[8];

@@ -6,6 +6,7 @@
 #pragma once
 #include "dil_keccak.cuh"
 #include "dil_keccak6.cuh"
+#include "dil_keccak16.cuh"
 #include "dil_ntt.cuh"
 
 namespace dil {
@@ -120,6 +121,92 @@ __device__ __forceinline__ void expand_a_six(const uint8_t *rho, int p0, int cou
         }
         if (!__any_sync(FULL, lane < count && mine < N)) break;
         keccak6_permute(kst, kpi);
+    }
+}
+
+// Sixteen-instance ExpandA: polynomials p0 .. p0 + count - 1 (count <= 16),
+// written like expand_a_six.  The candidates of two instances are voted on at
+// once, one per half-warp (4 x 16 candidate slots for a block's 56).
+template <int L>
+__device__ __forceinline__ void expand_a_16(const uint8_t *rho, int p0, int count, int32_t *out, uint32_t *kst,
+                                            int lane) {
+    keccak16_seed(
+        kst, reinterpret_cast<const uint32_t *>(rho), 8,
+        [&](int s) { const int p = p0 + s; return (uint32_t)(p % L) | ((uint32_t)(p / L) << 8) | (0x1Fu << 16); },
+        count, 168, lane);
+    keccak16_permute(kst);
+    const int half = lane >> 4, hl = lane & 15;
+    const uint32_t below = (1u << hl) - 1u;
+    int mine = 0;   // lane s < count: coefficients accepted so far for instance s
+#pragma unroll 1
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+#pragma unroll 1
+        for (int q = 0; 2 * q < count; ++q) {
+            const int s = 2 * q + half;
+            int c = __shfl_sync(FULL, mine, s);
+            const bool live = s < count && c < N;
+            if (!__any_sync(FULL, live)) continue;
+            int32_t *dst = out + s * N;
+#pragma unroll
+            for (int rnd = 0; rnd < 4; ++rnd) {
+                const int k = rnd * 16 + hl;
+                const int pos = 24 * k, w = pos >> 5;
+                const uint32_t lo = kst[k16_word(s, w)], hi = kst[k16_word(s, w + 1)];
+                const uint32_t v = __funnelshift_r(lo, hi, pos & 31) & 0x7FFFFFu;
+                const bool acc = live && k < 56 && v < (uint32_t)Q;
+                const uint32_t m = __ballot_sync(FULL, acc) >> (16 * half) & 0xFFFFu;
+                const int at = c + __popc(m & below);
+                if (acc && at < N) dst[at] = (int32_t)v;
+                c += __popc(m);
+            }
+            const int c_new = __shfl_sync(FULL, c, (lane & 1) << 4);
+            if ((lane >> 1) == q) mine = c_new;
+        }
+        if (!__any_sync(FULL, lane < count && mine < N)) break;
+        __syncwarp();
+        keccak16_permute(kst);
+    }
+    __syncwarp();
+}
+
+// Sixteen-instance ExpandMask: y for nonces nonce0 .. nonce0 + count - 1
+// (count <= 16), coefficient c of instance s at dst(s)[c] (natural order).
+// Fields whose last bit lies in the current block are extracted after each
+// permutation; the previous block's last lane (8 bytes, saved in `carry`, 32
+// words) supplies the start of a field that straddles two blocks.
+template <int ZBITS, int32_t GAMMA1, class Dst>
+__device__ __forceinline__ void expand_mask_16(const uint8_t *rhop, int nonce0, int count, Dst dst, uint32_t *kst,
+                                               uint32_t *carry, int lane) {
+    keccak16_seed(
+        kst, reinterpret_cast<const uint32_t *>(rhop), 16,
+        [&](int s) { return ((uint32_t)(nonce0 + s) & 0xFFFFu) | (0x1Fu << 16); }, count, 136, lane);
+    constexpr int BLOCKS = (N * ZBITS / 8 + 135) / 136;
+    const int half = lane >> 4, hl = lane & 15;
+    const uint32_t kst_a = smem_addr(kst), carry_a = smem_addr(carry);
+#pragma unroll 1
+    for (int b = 0; b < BLOCKS; ++b) {
+        if (b) {
+            carry[lane] = kst[32 * 16 + lane];   // lane 16: the block's last 8 bytes
+            __syncwarp();
+        }
+        keccak16_permute(kst);
+        const int c_lo = (1088 * b) / ZBITS;
+        const int c_hi = min(N, (1088 * (b + 1)) / ZBITS);
+#pragma unroll 1
+        for (int q = 0; 2 * q < count; ++q) {
+            const int s = 2 * q + half;
+            if (s >= count) continue;
+            int32_t *out = dst(s);
+            for (int c = c_lo + hl; c < c_hi; c += 16) {
+                // window word u: u < 2 the carry, else block word u - 2
+                const int pos = ZBITS * c - 1088 * b + 64, u = pos >> 5;
+                const uint32_t a0 = u < 2 ? carry_a + 4 * (2 * s + u) : kst_a + 4 * k16_word(s, u - 2);
+                const uint32_t a1 = u + 1 < 2 ? carry_a + 4 * (2 * s + u + 1) : kst_a + 4 * k16_word(s, u - 1);
+                const uint32_t f = __funnelshift_r(lds32(a0), lds32(a1), pos & 31) & ((1u << ZBITS) - 1u);
+                out[c] = GAMMA1 - (int32_t)f;
+            }
+        }
+        __syncwarp();
     }
 }
 

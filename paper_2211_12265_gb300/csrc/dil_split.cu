@@ -17,7 +17,9 @@ struct __align__(16) SplitState {
     uint8_t ctilde[32];
     int rep;      // current repetition index (nonce kappa = l rep)
     int done;     // 1 once signed or capped
-    int pad[6];
+    int ms_lo;    // the one-warp mask stream: nonces [ms_lo, ms_hi) sampled
+    int ms_hi;    // into the task's y ring by earlier rounds
+    int pad[4];
 };
 
 template <int LEVEL, int P>
@@ -55,6 +57,8 @@ __global__ void __launch_bounds__(256, 4) k_split_prepare(int n, const uint8_t *
         if (v.lane == 0) {
             st.rep = 0;
             st.done = 0;
+            st.ms_lo = 0;
+            st.ms_hi = 0;
         }
     }
 }
@@ -77,11 +81,16 @@ __global__ void __launch_bounds__(256, 4) k_split_front(int n, int32_t *scratch,
     }
     group_sync<P>(v.bar);
     int32_t *scr = scratch + (size_t)task * S::SIGN_POLYS * N;
-    MaskStream ms{0, 0};   // a round samples only its own repetition's masks
+    MaskStream ms{st.ms_lo, st.ms_hi};   // continues across rounds like the fused loop's
     const int kappa = Lv<LEVEL>::L * st.rep;
-    ms.lo = ms.hi = kappa;
     sign_front<LEVEL, P>(kappa, scr, scr + S::PRE_POLYS * N, ms, gs, *v.ws, v.zt, v.izt, v.g, v.bar, v.lane);
-    if (v.g == 0) st.ctilde[v.lane] = gs.ctilde[v.lane];
+    if (v.g == 0) {
+        st.ctilde[v.lane] = gs.ctilde[v.lane];
+        if (v.lane == 0) {
+            st.ms_lo = ms.lo;
+            st.ms_hi = ms.hi;
+        }
+    }
 }
 
 template <int LEVEL, int P>

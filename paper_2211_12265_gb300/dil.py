@@ -62,6 +62,7 @@ def load() -> ctypes.CDLL:
                 "dil_verify_host": [P, I, S, P, P, P, P, P, P],
                 "dil_test_shake": [P, I, S, P, P, P, S, P],
                 "dil_test_ntt": [P, S, P, P, I, P],
+                "dil_test_keccak_f": [P, I, S, P, P, P],
                 "dil_test_expand_a": [P, I, S, P, P, P],
                 "dil_test_expand_s": [P, I, S, P, P, P],
                 "dil_test_expand_mask": [P, I, S, P, P, P, P],
@@ -185,9 +186,10 @@ def dil_sign_noalloc(level, n, sk, msg, msg_off, sig, task_status=None, stream=N
 
 def _sign_scratch_polys(level: int) -> int:
     """Per-task scratch of the plain Sign kernel in polynomials: A^, s^1, s^2,
-    t^0, then the mask ring (l + 5), y^, w and z."""
+    t^0, then the mask ring (l + 15: masks are sampled sixteen nonces at a
+    time), y^, w and z."""
     k, l = {2: (4, 4), 3: (6, 5), 5: (8, 7)}[level]
-    return k * l + l + 2 * k + (l + 5) + l + k + l
+    return k * l + l + 2 * k + (l + 15) + l + k + l
 
 
 # Largest batch dil_sign_noalloc accepts: its 64 MiB static scratch over the
@@ -213,6 +215,11 @@ def dil_verify_host(ctx, level, n, pk, msg, msg_off, sig, ok, stream=None):
 def dil_test_shake(ctx, kind, n, inp, in_off, out, outlen, stream=None):
     return _check(load().dil_test_shake(ctx, kind, n, _ptr(inp), _ptr(in_off), _ptr(out), outlen,
                                         _stream(stream)), "dil_test_shake")
+
+
+def dil_test_keccak_f(ctx, form, n, inp, out, stream=None):
+    return _check(load().dil_test_keccak_f(ctx, int(form), n, _ptr(inp), _ptr(out), _stream(stream)),
+                  "dil_test_keccak_f")
 
 
 def dil_test_ntt(ctx, n, inp, out, inverse, stream=None):

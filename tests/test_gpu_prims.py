@@ -21,6 +21,25 @@ def ctx():
     c.close()
 
 
+@pytest.mark.parametrize("form", [1, 2, 6, 16])
+def test_keccak_f_forms(ctx, orc, form):
+    """Every permutation form against the oracle's Keccak-f[1600] on random
+    states, including a partly filled last warp (37 states) and the zero
+    state (whose image is a FIPS 202 constant the oracle is pinned to)."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    rng = np.random.default_rng(100 + form)
+    n = 37
+    st = rng.integers(0, 2 ** 64, (n, 25), dtype=np.uint64)
+    st[5] = 0
+    out = torch.empty((n, 25), dtype=torch.int64, device="cuda")
+    dil.dil_test_keccak_f(ctx.handle, form, n, dev(st.view(np.int64)), out)
+    got = host(out).view(np.uint64)
+    for i in range(n):
+        assert np.array_equal(got[i], orc.keccak_f1600(st[i])), (form, i)
+
+
 def test_shake_lengths(ctx, orc):
     import torch
     from gpu_util import dev, host
@@ -125,6 +144,8 @@ def test_probes_report_plausible_rates(ctx):
         assert 1.0 < r <= 128.0, (op, r)
     one = dil.dil_test_keccak_rate(ctx.handle, 1)
     six = dil.dil_test_keccak_rate(ctx.handle, 6)
+    sixteen = dil.dil_test_keccak_rate(ctx.handle, 16)
     assert 0.5 < six < one, (six, one)
+    assert 0.25 < sixteen < six, (sixteen, six)
     with pytest.raises(dil.DilError):
         dil.dil_test_keccak_rate(ctx.handle, 3)
