@@ -110,17 +110,31 @@ __device__ void commit(const PersistCtx &pc, PersistTask &tk, int r, const Persi
 }
 
 // Draws repetitions of task t until one accepts, the counter passes an
-// accepted r, or the cap is reached.  pre: the task's precomputation.
+// accepted r, or the cap is reached.  pre: the task's precomputation.  A
+// one-warp worker claims two consecutive repetitions at a time, so that the
+// second reuses masks its stream sampled for the first (one stream batch
+// covers MASK_BATCH / l repetitions; workers that share a task would
+// otherwise each start a new batch for every repetition); longer claims
+// reuse more masks but serialise more of a task's repetitions on one worker
+// and measured slower.  A worker abandons the rest of its claim once a
+// smaller repetition has accepted.
 template <int LEVEL, int P>
 __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const PersistJob &jb, int local,
                                 const int32_t *pre, int32_t *itr, GroupSmem &gs, WarpSmem &ws, const int32_t *zt,
                                 const int32_t *izt, int g, int bar, int lane) {
+    constexpr int PER_BATCH = Scratch<LEVEL>::MASK_BATCH / Lv<LEVEL>::L;
+    constexpr int CLAIM = (P == 1) ? (PER_BATCH < 2 ? PER_BATCH : 2) : 1;
     const int cap = iter_cap<LEVEL>(pc.max_iter_override);
     const bool leader = g == 0 && lane == 0;
     MaskStream ms{0, 0};
+    int next = 0, end = 0;   // the leader's current claim [next, end)
     for (;;) {
         if (leader) {
-            const int r = atomicAdd(&tk.next_r, 1);
+            if (next >= end) {
+                next = atomicAdd(&tk.next_r, CLAIM);
+                end = next + CLAIM;
+            }
+            const int r = next++;
             const int best = atomicOr(&tk.best_r, 0);
             const int canceled = ld_l2(&pc.q->cancel);
             gs.claim2 = (!canceled && r < cap && r < best) ? r : -1;
