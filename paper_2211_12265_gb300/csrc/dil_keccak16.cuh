@@ -12,8 +12,8 @@
 // fshl(v, m, r), r >= 32 gives fshl(m, v, r - 32)).  Per round that is 24
 // shuffles for rho and 5 for theta's rotation by one, about 125 instructions
 // per thread for 16 instances (about 8 warp instructions per instance-round,
-// against about 15 for the six-state row form and 66 for the 25-lane form),
-// and no shared-memory traffic inside the permutation.
+// against about 15 for the six-state row form and about 45 for the 25-lane
+// form), and no shared-memory traffic inside the permutation.
 //
 // Between permutations the states live in shared memory (`kst`, 800 words):
 // word i (lane i = x + 5y of the state) of thread `lane` at 32 i + lane, so
