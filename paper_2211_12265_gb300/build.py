@@ -39,15 +39,25 @@ def _deps() -> list[str]:
     return out
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace runs collapsed, so that
+    editing a comment does not change a digest."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_digest(unit: str = "dil_sign.cu") -> str:
-    """SHA-256 over one kernel translation unit and the device headers it
-    includes (ties a committed profile to the kernel version it measured)."""
+    """SHA-256 over the code (comments stripped) of one kernel translation
+    unit and the device headers it includes (ties a committed profile to the
+    kernel version it measured)."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
         if f.endswith(".cuh") or f == unit:
             h.update(f.encode())
-            h.update(open(os.path.join(CSRC, f), "rb").read())
+            h.update(_code_only(open(os.path.join(CSRC, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
