@@ -12,13 +12,16 @@
 // fshl(v, m, r), r >= 32 gives fshl(m, v, r - 32)).  Per round that is 24
 // shuffles for rho and 5 for theta's rotation by one, about 125 instructions
 // per thread for 16 instances (about 8 warp instructions per instance-round,
-// against about 15 for the six-state row form and about 45 for the 25-lane
-// form), and no shared-memory traffic inside the permutation.
+// against about 15 for the six-state row form and 66 for the 25-lane form),
+// and no shared-memory traffic inside the permutation.
 //
-// Between permutations the states live in shared memory (`kst`, 800 words):
-// word i (lane i = x + 5y of the state) of thread `lane` at 32 i + lane, so
-// every thread reaches its words without bank conflicts, and byte-stream
-// word w (4 bytes) of instance s sits at 32 (w >> 1) + 2 s + (w & 1).
+// Between permutations the states live in shared memory (`kst`, 850 words):
+// word i (lane i = x + 5y of the state) of thread `lane` at 34 i + lane, and
+// byte-stream word w (4 bytes) of instance s at 34 (w >> 1) + 2 s + (w & 1).
+// The two padding words per row put word w of an instance in bank
+// (w + 2 s) mod 32, so the samplers' reads of one instance's consecutive
+// stream words (16 lanes, a dozen words) do not conflict, while each thread's
+// own 25 words stay one per row at constant offsets.
 #pragma once
 #include "dil_keccak.cuh"
 #include "dil_ntt.cuh"
@@ -26,10 +29,13 @@
 namespace dil {
 
 constexpr int K16_STATES = 16;
-constexpr int K16_WORDS = 25 * 32;   // shared words of the sixteen states
+constexpr int K16_ROW = 34;                // words per state-word row (32 threads + 2 of padding)
+constexpr int K16_WORDS = 25 * K16_ROW;    // shared words of the sixteen states
 
+// Shared-memory word of state word i of thread `lane`.
+__host__ __device__ __forceinline__ int k16_slot(int i, int lane) { return K16_ROW * i + lane; }
 // Shared-memory word of byte-stream word w of instance s.
-__device__ __forceinline__ int k16_word(int s, int w) { return 32 * (w >> 1) + 2 * s + (w & 1); }
+__host__ __device__ __forceinline__ int k16_word(int s, int w) { return K16_ROW * (w >> 1) + 2 * s + (w & 1); }
 
 namespace detail {
 // FIPS 202 rho offset of lane (x, y).
@@ -72,7 +78,7 @@ static __device__ __noinline__ void keccak16_permute_impl(uint32_t kst) {
     const bool high = lane & 1;
     uint32_t a[25];
 #pragma unroll
-    for (int i = 0; i < 25; ++i) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[i]) : "r"(base + 128 * i));
+    for (int i = 0; i < 25; ++i) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[i]) : "r"(base + 4 * K16_ROW * i));
 #pragma unroll 1
     for (int round = 0; round < 24; ++round) {
         // theta
@@ -97,7 +103,8 @@ static __device__ __noinline__ void keccak16_permute_impl(uint32_t kst) {
         a[0] ^= high ? (uint32_t)(rc >> 32) : (uint32_t)rc;
     }
 #pragma unroll
-    for (int i = 0; i < 25; ++i) asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + 128 * i), "r"(a[i]) : "memory");
+    for (int i = 0; i < 25; ++i)
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + 4 * K16_ROW * i), "r"(a[i]) : "memory");
     __syncwarp();
 }
 
@@ -119,7 +126,7 @@ __device__ __forceinline__ void keccak16_seed(uint32_t *kst, const uint32_t *see
         const int w = 2 * i + p;
         uint32_t v = w < seed_words ? seed[w] : w == seed_words ? tail : 0u;
         if (w == rate / 4 - 1) v ^= 0x80000000u;
-        kst[32 * i + lane] = v;
+        kst[k16_slot(i, lane)] = v;
     }
     __syncwarp();
 }

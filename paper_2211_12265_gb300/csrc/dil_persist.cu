@@ -242,7 +242,10 @@ __device__ void help_task(const PersistCtx &pc, int t, const PersistJob &jb, int
                               lane);
 }
 
-template <int P>
+// ONLY = 0 compiles the task bodies of all three levels (launches that mix
+// levels); ONLY = 2, 3 or 5 compiles one level's, a smaller kernel with less
+// register pressure for the common single-level launch.
+template <int P, int ONLY>
 __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQueue *q, PersistTask *tasks,
                                                          int *slot_task, int32_t *scratch, int slot_polys,
                                                          int max_iter_override, int chunk, int spec) {
@@ -273,16 +276,25 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
             const PersistJob &jb = job_of(J, t, local);
             if (canceled) {
                 switch (jb.level) {
-                    case 2: mark_canceled<2, P>(jb, local, g, lane); break;
-                    case 3: mark_canceled<3, P>(jb, local, g, lane); break;
-                    default: mark_canceled<5, P>(jb, local, g, lane); break;
+                    case 2: if constexpr (ONLY == 0 || ONLY == 2) mark_canceled<2, P>(jb, local, g, lane); break;
+                    case 3: if constexpr (ONLY == 0 || ONLY == 3) mark_canceled<3, P>(jb, local, g, lane); break;
+                    default: if constexpr (ONLY == 0 || ONLY == 5) mark_canceled<5, P>(jb, local, g, lane); break;
                 }
                 continue;
             }
             switch (jb.level) {
-                case 2: own_task<2, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
-                case 3: own_task<3, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
-                default: own_task<5, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+                case 2:
+                    if constexpr (ONLY == 0 || ONLY == 2)
+                        own_task<2, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                    break;
+                case 3:
+                    if constexpr (ONLY == 0 || ONLY == 3)
+                        own_task<3, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                    break;
+                default:
+                    if constexpr (ONLY == 0 || ONLY == 5)
+                        own_task<5, P>(pc, t, jb, local, slot, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                    break;
             }
         }
     }
@@ -328,9 +340,18 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
         int local;
         const PersistJob &jb = job_of(J, t, local);
         switch (jb.level) {
-            case 2: help_task<2, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
-            case 3: help_task<3, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
-            default: help_task<5, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane); break;
+            case 2:
+                if constexpr (ONLY == 0 || ONLY == 2)
+                    help_task<2, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                break;
+            case 3:
+                if constexpr (ONLY == 0 || ONLY == 3)
+                    help_task<3, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                break;
+            default:
+                if constexpr (ONLY == 0 || ONLY == 5)
+                    help_task<5, P>(pc, t, jb, local, s, mine, gs, ws, v.zt, v.izt, g, bar, lane);
+                break;
         }
         __threadfence();
         group_sync<P>(bar);
@@ -353,29 +374,44 @@ int slot_polys_for(const PersistJobs &J) {
     return m + PERSIST_META_POLYS;
 }
 
-template <int P>
-cudaError_t grid_for(const PersistTuning &t, int device, int &grid) {
+using PersistKernel = void (*)(PersistJobs, PersistQueue *, PersistTask *, int *, int32_t *, int, int, int, int);
+
+// The kernel for a launch: one-warp groups whose jobs share one level get
+// that level's kernel, everything else the all-level one.
+PersistKernel kernel_for(const PersistJobs &J, int p) {
+    int only = J.job[0].level;
+    for (int j = 1; j < J.njobs; ++j)
+        if (J.job[j].level != only) only = 0;
+    if (p == 1) {
+        switch (only) {
+            case 2: return k_sign_persist<1, 2>;
+            case 3: return k_sign_persist<1, 3>;
+            case 5: return k_sign_persist<1, 5>;
+        }
+    }
+    switch (p) {
+        case 1: return k_sign_persist<1, 0>;
+        case 2: return k_sign_persist<2, 0>;
+        case 4: return k_sign_persist<4, 0>;
+    }
+    return nullptr;
+}
+
+cudaError_t grid_of(const PersistJobs &J, const PersistTuning &t, int device, int &grid) {
+    const PersistKernel kern = kernel_for(J, t.p);
+    if (!kern) return cudaErrorInvalidValue;
     int sms = 0, occ = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    const size_t smem = cta_bytes(t.warps, P);
-    e = cudaFuncSetAttribute(k_sign_persist<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = cta_bytes(t.warps, t.p);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sign_persist<P>, t.warps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, t.warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     int per_sm = (t.ctas_per_sm > 0 && t.ctas_per_sm < occ) ? t.ctas_per_sm : occ;
     grid = sms * per_sm;
     return cudaSuccess;
-}
-
-cudaError_t grid_of(const PersistTuning &t, int device, int &grid) {
-    switch (t.p) {
-        case 1: return grid_for<1>(t, device, grid);
-        case 2: return grid_for<2>(t, device, grid);
-        case 4: return grid_for<4>(t, device, grid);
-    }
-    return cudaErrorInvalidValue;
 }
 
 struct Layout {
@@ -384,7 +420,7 @@ struct Layout {
 };
 
 cudaError_t layout_of(const PersistJobs &J, const PersistTuning &t, int device, Layout &L) {
-    cudaError_t e = grid_of(t, device, L.grid);
+    cudaError_t e = grid_of(J, t, device, L.grid);
     if (e != cudaSuccess) return e;
     L.nslots = L.grid * (t.warps / t.p);
     L.slot_polys = slot_polys_for(J);
@@ -421,20 +457,9 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
     auto *scratch = reinterpret_cast<int32_t *>(base + L.scratch);
     const size_t smem = cta_bytes(t.warps, t.p);
     const int chunk = t.chunk > 0 ? t.chunk : 1;
-    switch (t.p) {
-        case 1:
-            k_sign_persist<1><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
-                                                                 max_iter_override, chunk, t.spec);
-            break;
-        case 2:
-            k_sign_persist<2><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
-                                                                 max_iter_override, chunk, t.spec);
-            break;
-        default:
-            k_sign_persist<4><<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys,
-                                                                 max_iter_override, chunk, t.spec);
-            break;
-    }
+    const PersistKernel kern = kernel_for(J, t.p);
+    kern<<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys, max_iter_override, chunk,
+                                            t.spec);
     return cudaGetLastError();
 }
 

@@ -96,14 +96,14 @@ __global__ void k_test_keccak_f(int n, int states, const uint64_t *in, uint64_t 
     } else {
         const int st = lane >> 1, h = lane & 1;
         for (int i = 0; i < 25; ++i)
-            ws.k16[32 * i + lane] = s0 + st < states ? (uint32_t)(in[(size_t)(s0 + st) * 25 + i] >> (32 * h)) : 0u;
+            ws.k16[k16_slot(i, lane)] = s0 + st < states ? (uint32_t)(in[(size_t)(s0 + st) * 25 + i] >> (32 * h)) : 0u;
         __syncwarp();
         keccak16_permute(ws.k16);
         for (int w = lane; w < K16_STATES * 25; w += 32) {
             const int g = w / 25, i = w % 25;
             if (s0 + g < states)
                 out[(size_t)(s0 + g) * 25 + i] =
-                    ((uint64_t)ws.k16[32 * i + 2 * g + 1] << 32) | ws.k16[32 * i + 2 * g];
+                    ((uint64_t)ws.k16[k16_slot(i, 2 * g + 1)] << 32) | ws.k16[k16_slot(i, 2 * g)];
         }
     }
 }

@@ -186,7 +186,7 @@ __device__ __forceinline__ void expand_mask_16(const uint8_t *rhop, int nonce0, 
 #pragma unroll 1
     for (int b = 0; b < BLOCKS; ++b) {
         if (b) {
-            carry[lane] = kst[32 * 16 + lane];   // lane 16: the block's last 8 bytes
+            carry[lane] = kst[k16_slot(16, lane)];   // lane 16: the block's last 8 bytes
             __syncwarp();
         }
         keccak16_permute(kst);
