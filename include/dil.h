@@ -299,6 +299,17 @@ int dil_test_shake(dil_ctx *ctx, int kind, size_t n, const uint8_t *in, const ui
  * interleaved states, 6 = six states in the skewed row layout, 16 = sixteen
  * states on two threads each.  DIL_EINVAL for another form. */
 int dil_test_keccak_f(dil_ctx *ctx, int form, size_t n, const uint64_t *in, uint64_t *out, void *stream);
+/* t^0 = NTT(t0) of n secret keys (n x SK bytes) -> n x k x 256 int32 in
+ * [0, q), index order: the paper's speedup breakdown of this step (section 5,
+ * "Speedup Breakdown").  variant 0: an unpack kernel and a transform kernel
+ * with t0 in global memory (the context workspace); 1: one fused kernel with
+ * the same global round trip; 2: one kernel with t0 in registers and an
+ * exchange layout with bank conflicts; 3: registers and the conflict-free
+ * layout, the form Sign uses.  All variants give the same output.
+ * DIL_EINVAL for another level or variant; DIL_ENOMEM when the workspace
+ * (variants 0, 1) exceeds the budget. */
+int dil_test_t0_ntt(dil_ctx *ctx, int level, int variant, size_t n, const uint8_t *sk, int32_t *t0hat,
+                    void *stream);
 /* Forward (inverse = 0) or inverse (inverse = 1) NTT of n polynomials of 256
  * int32 coefficients (any representatives with |a| < q); outputs in [0, q). */
 int dil_test_ntt(dil_ctx *ctx, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream);

@@ -728,6 +728,21 @@ int dil_test_keccak_f(dil_ctx *c, int form, size_t n, const uint64_t *in, uint64
     return status_of(dil::launch_test_keccak_f(form, (int)n, in, out, (cudaStream_t)stream));
 }
 
+int dil_test_t0_ntt(dil_ctx *c, int level, int variant, size_t n, const uint8_t *sk, int32_t *t0hat, void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || variant < 0 || variant > 3 || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!sk || !t0hat) return DIL_EINVAL;
+    int32_t *tmp = nullptr;
+    if (variant <= 1) {
+        const size_t k = level == 2 ? 4 : level == 3 ? 6 : 8;
+        const int rc = ensure_ws(c, n * k * POLY_BYTES);
+        if (rc) return rc;
+        tmp = static_cast<int32_t *>(c->ws);
+    }
+    return status_of(dil::launch_test_t0_ntt(level, variant, (int)n, sk, tmp, t0hat, (cudaStream_t)stream));
+}
+
 int dil_test_ntt(dil_ctx *c, size_t n, const int32_t *in, int32_t *out, int inverse, void *stream) {
     TEST_PROLOGUE(c)
     if (n > (size_t)INT32_MAX || (n && (!in || !out))) return DIL_EINVAL;

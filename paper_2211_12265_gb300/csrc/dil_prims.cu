@@ -124,6 +124,170 @@ __global__ void k_test_expand_a(int n, const uint8_t *rho, int32_t *out) {
     expand_a_range<LEVEL>(gs.rho, 9, V::K * V::L, o, ws, lane);
 }
 
+// ---------------------------------------------------------------- t^0 = NTT(t0)
+// The steps of the paper's speedup breakdown (section 5, computation of t^0
+// in Sign): unpack t0 from sk and transform it, as (0) an unpack kernel and a
+// transform kernel through global memory, (1) one fused kernel with the same
+// global-memory round trip, (2) one kernel keeping t0 in registers, with an
+// exchange layout that has bank conflicts, (3) registers and the
+// conflict-free layout (the form Sign uses).  Every variant writes the k
+// polynomials of t^0 per task in index order, reduced to [0, q).
+
+// Forward NTT with the exchanges unpadded (coefficient i at word i): the
+// L0 -> L1 reads and the L1 -> L2 writes put 8 lanes on one bank, the
+// L1 -> L2 reads 4.  Same arithmetic and output as ntt_fwd.
+static __device__ __noinline__ Poly8 ntt_fwd_unpadded_impl(Poly8 p, uint32_t buf, uint32_t zt) {
+    const int lane = threadIdx.x & 31;
+    int32_t *r = p.v;
+    {
+        const int32_t z = c_zetas.z[1];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ct_bfly(r[m], r[m + 4], z);
+    }
+    ct_bfly(r[0], r[2], c_zetas.z[2]);
+    ct_bfly(r[1], r[3], c_zetas.z[2]);
+    ct_bfly(r[4], r[6], c_zetas.z[3]);
+    ct_bfly(r[5], r[7], c_zetas.z[3]);
+    ct_bfly(r[0], r[1], c_zetas.z[4]);
+    ct_bfly(r[2], r[3], c_zetas.z[5]);
+    ct_bfly(r[4], r[5], c_zetas.z[6]);
+    ct_bfly(r[6], r[7], c_zetas.z[7]);
+    // L0 -> L1: coefficient t + 32 m, read back as 32 (t >> 2) + (t & 3) + 4 m
+#pragma unroll
+    for (int m = 0; m < 8; ++m) sts32(buf + 4 * (lane + 32 * m), r[m]);
+    __syncwarp();
+    const int b = lane >> 2;
+    const uint32_t base1 = buf + 4 * (32 * b + (lane & 3));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = lds32(base1 + 16 * m);
+    __syncwarp();
+    {
+        const int32_t z = ldz32(zt + 4 * (8 + b));
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ct_bfly(r[m], r[m + 4], z);
+    }
+    {
+        const int2 z = ldz64(zt + 4 * (16 + 2 * b));
+        ct_bfly(r[0], r[2], z.x);
+        ct_bfly(r[1], r[3], z.x);
+        ct_bfly(r[4], r[6], z.y);
+        ct_bfly(r[5], r[7], z.y);
+    }
+    {
+        const int4 z = ldz128(zt + 4 * (32 + 4 * b));
+        ct_bfly(r[0], r[1], z.x);
+        ct_bfly(r[2], r[3], z.y);
+        ct_bfly(r[4], r[5], z.z);
+        ct_bfly(r[6], r[7], z.w);
+    }
+    // L1 -> L2: back to coefficient order, read as 8 t + m
+#pragma unroll
+    for (int m = 0; m < 8; ++m) sts32(base1 + 16 * m, r[m]);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = lds32(buf + 4 * (8 * lane + m));
+    __syncwarp();
+    {
+        const int2 z = ldz64(zt + 4 * (64 + 2 * lane));
+        ct_bfly(r[0], r[2], z.x);
+        ct_bfly(r[1], r[3], z.x);
+        ct_bfly(r[4], r[6], z.y);
+        ct_bfly(r[5], r[7], z.y);
+    }
+    {
+        const int4 z = ldz128(zt + 4 * (128 + 4 * lane));
+        ct_bfly(r[0], r[1], z.x);
+        ct_bfly(r[2], r[3], z.y);
+        ct_bfly(r[4], r[5], z.z);
+        ct_bfly(r[6], r[7], z.w);
+    }
+    return p;
+}
+
+template <int LEVEL>
+__device__ __forceinline__ void t0_unpack(int32_t r[8], const uint8_t *sk, int i, WarpSmem &ws, int lane) {
+    using V = Lv<LEVEL>;
+    unpack_poly_l0<D>(r, sk + V::SK_T0 + i * V::POLYT0, 1 << (D - 1), ws, lane);
+}
+
+__device__ __forceinline__ void t0_store(int32_t *dst, int32_t r[8], int lane) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = to_canonical(reduce_q(r[m]));
+    store_l2(dst, r, lane);
+}
+
+// (0a) unpack kernel: t0 of task `item` to tmp (natural order)
+template <int LEVEL>
+__global__ void k_test_t0_unpack(int n, const uint8_t *sk, int32_t *tmp) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    int32_t r[8];
+#pragma unroll 1
+    for (int i = 0; i < V::K; ++i) {
+        t0_unpack<LEVEL>(r, sk + (size_t)item * V::SK, i, ws, lane);
+        store_l0(tmp + ((size_t)item * V::K + i) * N, r, lane);
+    }
+}
+
+// (0b) transform kernel: tmp -> t^0
+template <int LEVEL>
+__global__ void k_test_t0_ntt(int n, const int32_t *tmp, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    int32_t r[8];
+#pragma unroll 1
+    for (int i = 0; i < V::K; ++i) {
+        load_l0(r, tmp + ((size_t)item * V::K + i) * N, lane);
+        ntt_fwd(r, ws.buf, zt, lane);
+        t0_store(out + ((size_t)item * V::K + i) * N, r, lane);
+    }
+}
+
+// (1) both steps in one kernel, t0 still through global memory
+template <int LEVEL>
+__global__ void k_test_t0_fused_gmem(int n, const uint8_t *sk, int32_t *tmp, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    int32_t r[8];
+    int32_t *t = tmp + (size_t)item * V::K * N;
+#pragma unroll 1
+    for (int i = 0; i < V::K; ++i) {
+        t0_unpack<LEVEL>(r, sk + (size_t)item * V::SK, i, ws, lane);
+        store_l0(t + i * N, r, lane);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int i = 0; i < V::K; ++i) {
+        load_l0(r, t + i * N, lane);
+        ntt_fwd(r, ws.buf, zt, lane);
+        t0_store(out + ((size_t)item * V::K + i) * N, r, lane);
+    }
+}
+
+// (2) / (3) one kernel, t0 in registers; UNPADDED selects the conflicting
+// exchange layout
+template <int LEVEL, bool UNPADDED>
+__global__ void k_test_t0_registers(int n, const uint8_t *sk, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    int32_t r[8];
+#pragma unroll 1
+    for (int i = 0; i < V::K; ++i) {
+        t0_unpack<LEVEL>(r, sk + (size_t)item * V::SK, i, ws, lane);
+        if constexpr (UNPADDED) {
+            Poly8 p;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) p.v[m] = r[m];
+            p = ntt_fwd_unpadded_impl(p, smem_addr(ws.buf), smem_addr(zt));
+#pragma unroll
+            for (int m = 0; m < 8; ++m) r[m] = p.v[m];
+        } else {
+            ntt_fwd(r, ws.buf, zt, lane);
+        }
+        t0_store(out + ((size_t)item * V::K + i) * N, r, lane);
+    }
+}
+
 template <int LEVEL>
 __global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
     PRIM_PROLOGUE
@@ -238,6 +402,29 @@ cudaError_t launch_test_keccak_f(int form, int states, const uint64_t *in, uint6
         case 2: return launch_prim(k_test_keccak_f<2>, items, s, states, in, out);
         case 6: return launch_prim(k_test_keccak_f<6>, items, s, states, in, out);
         case 16: return launch_prim(k_test_keccak_f<16>, items, s, states, in, out);
+    }
+    return cudaErrorInvalidValue;
+}
+template <int LEVEL>
+static cudaError_t launch_t0_variant(int variant, int n, const uint8_t *sk, int32_t *tmp, int32_t *out,
+                                     cudaStream_t s) {
+    switch (variant) {
+        case 0: {
+            cudaError_t e = launch_prim(k_test_t0_unpack<LEVEL>, n, s, sk, tmp);
+            return e != cudaSuccess ? e : launch_prim(k_test_t0_ntt<LEVEL>, n, s, (const int32_t *)tmp, out);
+        }
+        case 1: return launch_prim(k_test_t0_fused_gmem<LEVEL>, n, s, sk, tmp, out);
+        case 2: return launch_prim(k_test_t0_registers<LEVEL, true>, n, s, sk, out);
+        case 3: return launch_prim(k_test_t0_registers<LEVEL, false>, n, s, sk, out);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_test_t0_ntt(int level, int variant, int n, const uint8_t *sk, int32_t *tmp, int32_t *out,
+                               cudaStream_t s) {
+    switch (level) {
+        case 2: return launch_t0_variant<2>(variant, n, sk, tmp, out, s);
+        case 3: return launch_t0_variant<3>(variant, n, sk, tmp, out, s);
+        case 5: return launch_t0_variant<5>(variant, n, sk, tmp, out, s);
     }
     return cudaErrorInvalidValue;
 }

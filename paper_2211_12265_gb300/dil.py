@@ -63,6 +63,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_shake": [P, I, S, P, P, P, S, P],
                 "dil_test_ntt": [P, S, P, P, I, P],
                 "dil_test_keccak_f": [P, I, S, P, P, P],
+                "dil_test_t0_ntt": [P, I, I, S, P, P, P],
                 "dil_test_expand_a": [P, I, S, P, P, P],
                 "dil_test_expand_s": [P, I, S, P, P, P],
                 "dil_test_expand_mask": [P, I, S, P, P, P, P],
@@ -220,6 +221,11 @@ def dil_test_shake(ctx, kind, n, inp, in_off, out, outlen, stream=None):
 def dil_test_keccak_f(ctx, form, n, inp, out, stream=None):
     return _check(load().dil_test_keccak_f(ctx, int(form), n, _ptr(inp), _ptr(out), _stream(stream)),
                   "dil_test_keccak_f")
+
+
+def dil_test_t0_ntt(ctx, level, variant, n, sk, out, stream=None):
+    return _check(load().dil_test_t0_ntt(ctx, int(level), int(variant), n, _ptr(sk), _ptr(out), _stream(stream)),
+                  "dil_test_t0_ntt")
 
 
 def dil_test_ntt(ctx, n, inp, out, inverse, stream=None):

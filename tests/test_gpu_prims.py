@@ -149,3 +149,36 @@ def test_probes_report_plausible_rates(ctx):
     assert 0.25 < sixteen < six, (sixteen, six)
     with pytest.raises(dil.DilError):
         dil.dil_test_keccak_rate(ctx.handle, 3)
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_t0_ntt_breakdown_variants(ctx, orc, level):
+    """The four forms of the t^0 = NTT(t0) breakdown (two kernels through
+    global memory, fused, registers with a conflicting exchange, registers
+    with the conflict-free one) give the same t^0, equal to the oracle's NTT
+    of t0 unpacked from sk."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    from paper_2211_12265_gb300 import workload as W
+    n = 300
+    k = {2: 4, 3: 6, 5: 8}[level]
+    _, sk = ctx.keygen(level, dev(W.seeds(n, 60 + level)))
+    outs = []
+    for variant in range(4):
+        out = torch.full((n, k, 256), -1, dtype=torch.int32, device="cuda")
+        dil.dil_test_t0_ntt(ctx.handle, level, variant, n, sk, out)
+        outs.append(host(out))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    skh = host(sk)
+    eta_bits = 3 if level in (2, 5) else 4
+    l = {2: 4, 3: 5, 5: 7}[level]
+    t0_at = 96 + (k + l) * 32 * eta_bits
+    for i in range(0, n, 7):
+        for j in range(k):
+            field = orc.unpack_bits(skh[i, t0_at + 416 * j: t0_at + 416 * (j + 1)].tobytes(), 256, 13)
+            t0 = (4096 - field.astype(np.int64)) % Q
+            assert np.array_equal(outs[3][i, j], orc.ntt(t0)), (i, j)
+    with pytest.raises(dil.DilError):
+        dil.dil_test_t0_ntt(ctx.handle, level, 4, n, sk, out)
