@@ -219,7 +219,8 @@ typedef struct {
     int32_t op;          /* 0 = sign, 1 = verify */
     int32_t level;
     int32_t status;      /* sign: DIL_OK, DIL_EITER or DIL_EINVAL (unknown key); any op:
-                            DIL_ECUDA when the batch's copies or kernels failed */
+                            DIL_ECUDA when the batch's copies or kernels failed,
+                            DIL_ECANCELED when dil_server_cancel withdrew it */
     uint8_t ok;          /* verify: 1 = accept */
     uint8_t sig[4595];   /* sign: the signature (first SIG bytes) */
     double latency_s;    /* arrival to result visible on the host */
@@ -254,6 +255,12 @@ int dil_server_add_keys(dil_server *srv, int level, size_t n, const uint8_t *pk,
  * key `key`); the message (and signature) are copied.  *id identifies it. */
 int dil_server_submit(dil_server *srv, int op, int level, int32_t key, const uint8_t *msg, size_t mlen,
                       const uint8_t *sig, uint64_t *id);
+/* Withdraws submitted request `id` while it is still pending (not yet taken
+ * into a batch): it completes at once with status DIL_ECANCELED (ok 0, no
+ * signature) and is returned by dil_server_poll like any other.  DIL_EINVAL
+ * when the id is unknown or the request was already dispatched (it then
+ * completes normally). */
+int dil_server_cancel(dil_server *srv, uint64_t id);
 /* Returns up to max_n completed submitted requests (waiting up to wait_us for
  * the first one); *n_out receives the count. */
 int dil_server_poll(dil_server *srv, dil_result *out, size_t max_n, size_t *n_out, int wait_us);

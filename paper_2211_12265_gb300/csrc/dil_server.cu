@@ -502,6 +502,24 @@ int dil_server_submit(dil_server *sv, int op, int level, int32_t key, const uint
     return DIL_OK;
 }
 
+int dil_server_cancel(dil_server *sv, uint64_t id) {
+    if (!sv) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto it = sv->pending.begin(); it != sv->pending.end(); ++it) {
+        Req *r = *it;
+        if (r->id != id || !r->owned) continue;
+        sv->pending.erase(it);
+        r->res.status = DIL_ECANCELED;
+        r->res.ok = 0;
+        r->res.latency_s = now_s() - r->t_arrive;
+        sv->completed.push_back(r);
+        sv->outstanding--;
+        sv->cv_done.notify_all();
+        return DIL_OK;
+    }
+    return DIL_EINVAL;   // unknown, already dispatched or completed
+}
+
 int dil_server_poll(dil_server *sv, dil_result *out, size_t max_n, size_t *n_out, int wait_us) {
     if (!sv || !out || !n_out) return DIL_EINVAL;
     std::unique_lock<std::mutex> lk(sv->mu);

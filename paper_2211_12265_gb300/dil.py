@@ -89,6 +89,7 @@ def load() -> ctypes.CDLL:
                 "dil_server_add_keys": [P, I, S, P, P],
                 "dil_server_submit": [P, I, I, ctypes.c_int32, P, S, P, P],
                 "dil_server_poll": [P, P, S, P, I],
+                "dil_server_cancel": [P, ctypes.c_uint64],
                 "dil_server_replay": [P, S, P, P, P, P, P, P, P, P, P, P, P, P],
                 "dil_server_stats": [P, P, P, P],
             }
@@ -381,6 +382,12 @@ def dil_server_submit(srv, op, level, key, msg: bytes, sig: bytes | None = None)
     sg = (ctypes.c_uint8 * len(sig)).from_buffer_copy(sig) if sig is not None else None
     _check(load().dil_server_submit(srv, op, level, key, m, len(msg), sg, ctypes.byref(rid)), "dil_server_submit")
     return rid.value
+
+
+def dil_server_cancel(srv, rid: int) -> int:
+    """DIL_OK when request `rid` was still pending and is now canceled, else
+    DIL_EINVAL (unknown or already dispatched); does not raise."""
+    return load().dil_server_cancel(srv, rid)
 
 
 def dil_server_poll(srv, max_n=256, wait_us=1000) -> list:

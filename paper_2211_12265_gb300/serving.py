@@ -49,6 +49,10 @@ class Server:
     def submit(self, op: int, level: int, key: int, msg: bytes, sig: bytes | None = None) -> int:
         return dil.dil_server_submit(self.handle, op, level, key, msg, sig)
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a still-pending request; True when it was canceled."""
+        return dil.dil_server_cancel(self.handle, rid) == dil.OK
+
     def poll(self, max_n: int = 256, wait_us: int = 1000) -> list:
         return dil.dil_server_poll(self.handle, max_n, wait_us)
 

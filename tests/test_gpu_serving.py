@@ -131,3 +131,42 @@ def test_server_policies_and_shapes_agree(keys):
         assert np.array_equal(base["sig"][sign], other["sig"][sign])
         assert np.array_equal(base["status"], other["status"]) and (base["status"][sign] == 0).all()
         assert np.array_equal(base["ok"][~sign], other["ok"][~sign]) and base["ok"][~sign].all()
+
+
+def test_server_cancel_pending_requests(keys):
+    """Requests held back by a static batching policy can be withdrawn: they
+    complete at once with DIL_ECANCELED; the others complete normally with the
+    signatures dil_sign gives; unknown and completed ids are refused."""
+    import torch
+    from paper_2211_12265_gb300 import dil, serving
+    pk, sk = keys[2]
+    n = 20
+    msgs = [bytes([i]) * (10 + i) for i in range(n)]
+    with serving.Server(0, memory_budget=256 << 20, streams=2, max_batch=64) as srv:
+        srv.add_keys(2, pk, sk)
+        srv.set_batching(10_000, 30.0)            # hold everything back
+        ids = [srv.submit(0, 2, i % pk.shape[0], msgs[i]) for i in range(n)]
+        canceled = set(ids[::2])
+        for rid in sorted(canceled):
+            assert srv.cancel(rid)
+        assert not srv.cancel(max(ids) + 1000)    # unknown id
+        srv.set_batching(1, 0.0)                  # release the rest
+        got = {}
+        while len(got) < n:
+            for r in srv.poll(64, 200000):
+                got[r.id] = (r.status, bytes(r.sig)[:2420])
+        assert not srv.cancel(ids[1])             # already completed
+    off = np.zeros(n + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(m) for m in msgs])
+    msg = np.frombuffer(b"".join(msgs), dtype=np.uint8)
+    kidx = np.arange(n) % pk.shape[0]
+    with dil.Context(0) as ctx:
+        ref, st = ctx.sign(2, torch.from_numpy(sk[kidx]).cuda(), torch.from_numpy(msg.copy()).cuda(),
+                           torch.from_numpy(off).cuda())
+        ref = ref.cpu().numpy()
+    for i, rid in enumerate(ids):
+        status, sig = got[rid]
+        if rid in canceled:
+            assert status == dil.ECANCELED
+        else:
+            assert status == dil.OK and sig == ref[i].tobytes()
