@@ -330,6 +330,12 @@ int dil_test_expand_mask(dil_ctx *ctx, int level, size_t n, const uint8_t *rhop,
 /* SampleInBall of n seeds c~ (n x 32 bytes) -> n x 256 int32 in {-1, 0, 1}. */
 int dil_test_sample_in_ball(dil_ctx *ctx, int level, size_t n, const uint8_t *ctilde, int32_t *c,
                             void *stream);
+/* SampleInBall's drawing and swapping over given bytes instead of
+ * SHAKE256(c~): per task `blocks` (1..64) blocks of 136 bytes (n x blocks x
+ * 136, device), the first starting with the 8 sign bytes; a task that needs
+ * more blocks reuses the last one.  Output as dil_test_sample_in_ball. */
+int dil_test_sample_in_ball_stream(dil_ctx *ctx, int level, size_t n, const uint8_t *bytes, int blocks, int32_t *cc,
+                                   void *stream);
 /* Coefficient functions of section 2.3 on n values r in [0, q) (and z, h):
  * out is n x 6 int32: Power2Round (r1, r0), Decompose (r1, r0),
  * MakeHint(z, r), UseHint(h, r). */

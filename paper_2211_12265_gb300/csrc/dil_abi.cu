@@ -768,6 +768,14 @@ int dil_test_expand_mask(dil_ctx *c, int level, size_t n, const uint8_t *rhop, c
     return status_of(dil::launch_test_expand_mask(level, (int)n, rhop, kappa, y, (cudaStream_t)stream));
 }
 
+int dil_test_sample_in_ball_stream(dil_ctx *c, int level, size_t n, const uint8_t *bytes, int blocks, int32_t *cc,
+                                   void *stream) {
+    TEST_PROLOGUE(c)
+    if (!level_ok(level) || n > (size_t)INT32_MAX || blocks < 1 || blocks > 64 || (n && (!bytes || !cc)))
+        return DIL_EINVAL;
+    return status_of(dil::launch_test_sib_stream(level, (int)n, bytes, blocks, cc, (cudaStream_t)stream));
+}
+
 int dil_test_sample_in_ball(dil_ctx *c, int level, size_t n, const uint8_t *ctilde, int32_t *cc, void *stream) {
     TEST_PROLOGUE(c)
     if (!level_ok(level) || n > (size_t)INT32_MAX || (n && (!ctilde || !cc))) return DIL_EINVAL;

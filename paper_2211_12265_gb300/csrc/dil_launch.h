@@ -63,6 +63,8 @@ cudaError_t launch_test_expand_s(int level, int n, const uint8_t *rhop, int32_t 
 cudaError_t launch_test_expand_mask(int level, int n, const uint8_t *rhop, const int32_t *kappa, int32_t *out,
                                     cudaStream_t s);
 cudaError_t launch_test_sample_in_ball(int level, int n, const uint8_t *ct, int32_t *out, cudaStream_t s);
+cudaError_t launch_test_sib_stream(int level, int n, const uint8_t *stream, int blocks, int32_t *out,
+                                   cudaStream_t s);
 cudaError_t launch_test_rounding(int level, int n, const int32_t *r, const int32_t *z, const uint8_t *h,
                                  int32_t *out, cudaStream_t s);
 

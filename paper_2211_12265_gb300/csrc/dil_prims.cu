@@ -354,6 +354,30 @@ __global__ void k_test_sample_in_ball(int n, const uint8_t *ct, int32_t *out) {
     store_l0(out + (size_t)item * N, a, lane);
 }
 
+// SampleInBall over a given byte stream of `blocks` 136-byte blocks per item
+// (the first starting with the 8 sign bytes) instead of SHAKE256(c~), so that
+// tests can feed streams that reject many bytes and cross block boundaries.
+template <int LEVEL>
+__global__ void k_test_sib_stream(int n, const uint8_t *stream, int blocks, int32_t *out) {
+    PRIM_PROLOGUE
+    using V = Lv<LEVEL>;
+    const uint8_t *src = stream + (size_t)item * blocks * 136;
+    for (int i = lane; i < 136; i += 32) ws.sq[i] = src[i];
+    __syncwarp();
+    int next = 1;
+    sample_in_ball_blocks<V::TAU>(
+        ws.buf, ws.sq,
+        [&](uint8_t *dst) {
+            const uint8_t *b = src + (size_t)min(next, blocks - 1) * 136;   // past the end: repeat the last
+            for (int i = lane; i < 136; i += 32) dst[i] = b[i];
+            ++next;
+        },
+        lane);
+    int32_t a[8];
+    read_buf_l0(a, ws.buf, lane);
+    store_l0(out + (size_t)item * N, a, lane);
+}
+
 template <int LEVEL>
 __global__ void k_test_rounding(int n, const int32_t *r, const int32_t *z, const uint8_t *h, int32_t *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -440,6 +464,10 @@ cudaError_t launch_test_expand_mask(int level, int n, const uint8_t *rhop, const
 }
 cudaError_t launch_test_sample_in_ball(int level, int n, const uint8_t *ct, int32_t *out, cudaStream_t s) {
     BY_LEVEL(k_test_sample_in_ball, ct, out)
+}
+cudaError_t launch_test_sib_stream(int level, int n, const uint8_t *stream, int blocks, int32_t *out,
+                                   cudaStream_t s) {
+    BY_LEVEL(k_test_sib_stream, stream, blocks, out)
 }
 cudaError_t launch_test_rounding(int level, int n, const int32_t *r, const int32_t *z, const uint8_t *h,
                                  int32_t *out, cudaStream_t s) {

@@ -360,40 +360,133 @@ __device__ __forceinline__ void expand_mask_pair(const uint8_t *rhop, int nonce0
 
 // ---------------------------------------------------------------- SampleInBall
 // c with TAU coefficients +-1 from SHAKE256(c~): the first 8 bytes give the
-// signs, then for i = 256-TAU .. 255 a byte b <= i is drawn, c_i <- c_b and
-// c_b <- +-1.  Coefficient c is written to buf[c + 4 (c >> 5)].
+// signs, then for step k = 0 .. TAU-1 (i = 256 - TAU + k) a byte b <= i is
+// drawn, c_i <- c_b and c_b <- (-1)^(sign bit k).  Coefficient c is written to
+// buf[c + 4 (c >> 5)].
+//
+// The steps are sequential by definition; the warp evaluates them in
+// parallel with the same result:
+//  1. Which bytes are drawn.  Byte l of a 32-byte chunk is taken iff
+//     b_l <= i0 + A_l, A_l the number taken among the bytes before it.  Start
+//     from "all taken" and recompute the takes from the prefix counts until
+//     nothing changes: the sets only shrink, never below the sequential
+//     answer, and each pass settles at least the first wrong byte, so the
+//     (unique) fixed point is the sequential result after at most 33 passes.
+//  2. Where each position ends.  Step k writes position i_k (the value of
+//     position b_k before the step) and then position b_k (its sign).  A
+//     step that writes p as b_k comes at or after the step whose i is p, so
+//     the final c_p is the sign of the last step with b_k = p, else, for
+//     p = i_k, the value step k moved there, else 0.  That moved value is the
+//     same rule applied before step k: the sign of the last earlier step with
+//     b_j = b_k, else the value moved by the earlier step whose i is b_k, else
+//     0 — a chain resolved by pointer jumping.
+// next_block(sq) refills sq[0 .. 136) with the next squeezed block.
+template <int TAU, class NextBlock>
+__device__ __forceinline__ void sample_in_ball_blocks(int32_t *buf, uint8_t *sq, NextBlock next_block, int lane) {
+    static_assert(TAU <= 64, "two steps per lane");
+    uint8_t *bk = sq + 136;                              // b_k of step k
+    int8_t *vk = reinterpret_cast<int8_t *>(sq + 200);   // value moved into i_k by step k
+    const uint64_t signs = *reinterpret_cast<const unsigned long long *>(sq);
+    const uint32_t below = (1u << lane) - 1u;
+    // 1. the drawn bytes
+    int taken = 0, pos = 8, blocks = 1;
+#pragma unroll 1
+    while (taken < TAU) {
+        if (pos == 136) {
+            if (++blocks > MAX_SQUEEZE_BLOCKS) break;
+            __syncwarp();
+            next_block(sq);
+            __syncwarp();
+            pos = 0;
+        }
+        const int cnt = min(32, 136 - pos);
+        const int b = lane < cnt ? (int)sq[pos + lane] : N;
+        uint32_t acc = __ballot_sync(FULL, lane < cnt);
+#pragma unroll 1
+        for (int pass = 0; pass <= 32; ++pass) {
+            const int before = taken + __popc(acc & below);
+            const uint32_t m = __ballot_sync(FULL, lane < cnt && before < TAU && b <= N - TAU + before);
+            if (m == acc) break;
+            acc = m;
+        }
+        if ((acc >> lane) & 1u) bk[taken + __popc(acc & below)] = (uint8_t)b;
+        taken += __popc(acc);
+        pos += cnt;
+    }
+    // 2. the last step writing each position as a b_k (buf holds it for now)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) buf[lane + 36 * m] = -1;
+    __syncwarp();
+    const int k0 = lane, k1 = lane + 32;
+    const int b0 = k0 < taken ? (int)bk[k0] : -1, b1 = k1 < taken ? (int)bk[k1] : -1;
+    if (b0 >= 0) atomicMax(&buf[b0 + 4 * (b0 >> 5)], k0);
+    if (b1 >= 0) atomicMax(&buf[b1 + 4 * (b1 >> 5)], k1);
+    // the last earlier step with the same b
+    int lb0 = -1, lb1 = -1;
+#pragma unroll 1
+    for (int j = 0; j < taken; ++j) {
+        const int bj = __shfl_sync(FULL, j < 32 ? b0 : b1, j & 31);
+        if (j < k0 && bj == b0) lb0 = j;
+        if (j < k1 && bj == b1) lb1 = j;
+    }
+    // moved values: resolved (r < 0) or equal to step r's
+    auto sign_of = [&](int k) { return ((signs >> k) & 1ull) ? -1 : 1; };
+    int v0 = 0, v1 = 0, r0 = -1, r1 = -1;
+    if (k0 < taken) {
+        if (lb0 >= 0) v0 = sign_of(lb0);
+        else if (b0 >= N - TAU && b0 - (N - TAU) < k0) r0 = b0 - (N - TAU);
+    }
+    if (k1 < taken) {
+        if (lb1 >= 0) v1 = sign_of(lb1);
+        else if (b1 >= N - TAU && b1 - (N - TAU) < k1) r1 = b1 - (N - TAU);
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < TAU; ++pass) {
+        if (!__any_sync(FULL, r0 >= 0 || r1 >= 0)) break;
+        const int s0 = r0 >= 0 ? r0 : 0, s1 = r1 >= 0 ? r1 : 0;
+        const int a0v = __shfl_sync(FULL, v0, s0 & 31), a1v = __shfl_sync(FULL, v1, s0 & 31);
+        const int a0r = __shfl_sync(FULL, r0, s0 & 31), a1r = __shfl_sync(FULL, r1, s0 & 31);
+        const int c0v = __shfl_sync(FULL, v0, s1 & 31), c1v = __shfl_sync(FULL, v1, s1 & 31);
+        const int c0r = __shfl_sync(FULL, r0, s1 & 31), c1r = __shfl_sync(FULL, r1, s1 & 31);
+        if (r0 >= 0) {
+            v0 = s0 < 32 ? a0v : a1v;
+            r0 = s0 < 32 ? a0r : a1r;
+        }
+        if (r1 >= 0) {
+            v1 = s1 < 32 ? c0v : c1v;
+            r1 = s1 < 32 ? c0r : c1r;
+        }
+    }
+    if (k0 < taken) vk[k0] = (int8_t)v0;
+    if (k1 < taken) vk[k1] = (int8_t)v1;
+    __syncwarp();
+    // 3. final coefficients (lane t owns positions t + 32 m)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int p = lane + 32 * m, last = buf[lane + 36 * m];
+        int c = 0;
+        if (last >= 0)
+            c = sign_of(last);
+        else if (p >= N - TAU && p - (N - TAU) < taken)
+            c = vk[p - (N - TAU)];
+        buf[lane + 36 * m] = c;
+    }
+    __syncwarp();
+}
+
 template <int TAU>
 __device__ __forceinline__ void sample_in_ball(const uint8_t *ctilde, int32_t *buf, uint8_t *sq, int lane) {
     uint32_t lo, hi;
     absorb_seed(lo, hi, ctilde, 4, 0u, 0, 136, lane);
     squeeze_words(lo, hi, sq, 17, lane);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) buf[lane + 36 * m] = 0;
     __syncwarp();
-    uint64_t signs = *reinterpret_cast<const unsigned long long *>(sq);
-    int pos = 8, blocks = 1;
-#pragma unroll 1
-    for (int i = N - TAU; i < N; ++i) {
-        int b;
-        do {
-            if (pos == 136) {
-                if (++blocks > MAX_SQUEEZE_BLOCKS) break;
-                __syncwarp();
-                keccak_f(lo, hi);
-                squeeze_words(lo, hi, sq, 17, lane);
-                __syncwarp();
-                pos = 0;
-            }
-            b = sq[pos++];
-        } while (b > i);
-        if (lane == 0) {
-            int32_t cb = buf[b + 4 * (b >> 5)];
-            buf[i + 4 * (i >> 5)] = cb;
-            buf[b + 4 * (b >> 5)] = (signs & 1) ? -1 : 1;
-        }
-        signs >>= 1;
-    }
-    __syncwarp();
+    sample_in_ball_blocks<TAU>(
+        buf, sq,
+        [&](uint8_t *dst) {
+            keccak_f(lo, hi);
+            squeeze_words(lo, hi, dst, 17, lane);
+        },
+        lane);
 }
 
 // ---------------------------------------------------------------- packing

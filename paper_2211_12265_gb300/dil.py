@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_ntt": [P, S, P, P, I, P],
                 "dil_test_keccak_f": [P, I, S, P, P, P],
                 "dil_test_t0_ntt": [P, I, I, S, P, P, P],
+                "dil_test_sample_in_ball_stream": [P, I, S, P, I, P, P],
                 "dil_test_expand_a": [P, I, S, P, P, P],
                 "dil_test_expand_s": [P, I, S, P, P, P],
                 "dil_test_expand_mask": [P, I, S, P, P, P, P],
@@ -222,6 +223,11 @@ def dil_test_shake(ctx, kind, n, inp, in_off, out, outlen, stream=None):
 def dil_test_keccak_f(ctx, form, n, inp, out, stream=None):
     return _check(load().dil_test_keccak_f(ctx, int(form), n, _ptr(inp), _ptr(out), _stream(stream)),
                   "dil_test_keccak_f")
+
+
+def dil_test_sample_in_ball_stream(ctx, level, n, data, blocks, out, stream=None):
+    return _check(load().dil_test_sample_in_ball_stream(ctx, int(level), n, _ptr(data), int(blocks), _ptr(out),
+                                                        _stream(stream)), "dil_test_sample_in_ball_stream")
 
 
 def dil_test_t0_ntt(ctx, level, variant, n, sk, out, stream=None):

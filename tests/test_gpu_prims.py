@@ -182,3 +182,74 @@ def test_t0_ntt_breakdown_variants(ctx, orc, level):
             assert np.array_equal(outs[3][i, j], orc.ntt(t0)), (i, j)
     with pytest.raises(dil.DilError):
         dil.dil_test_t0_ntt(ctx.handle, level, 4, n, sk, out)
+
+
+def _sib_reference(blocks, tau):
+    """SampleInBall's drawing and swapping (section 2.3) over a given byte
+    stream, one step at a time; past the last block the last one repeats."""
+    signs = int.from_bytes(bytes(blocks[0][:8]), "little")
+    c = [0] * 256
+    state = {"blk": 0, "pos": 8}
+
+    def next_byte():
+        if state["pos"] == 136:
+            state["blk"] += 1
+            state["pos"] = 0
+        b = int(blocks[min(state["blk"], len(blocks) - 1)][state["pos"]])
+        state["pos"] += 1
+        return b
+
+    for k, i in enumerate(range(256 - tau, 256)):
+        while True:
+            b = next_byte()
+            if b <= i:
+                break
+        c[i] = c[b]
+        c[b] = -1 if (signs >> k) & 1 else 1
+    return np.array(c, dtype=np.int32)
+
+
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_sample_in_ball_adversarial_streams(ctx, level):
+    """The warp-parallel SampleInBall against the sequential definition on
+    streams built to stress it: heavy rejection, a first block rejected
+    entirely (the draw continues in the next block), repeated positions
+    (values moved several times), b = i, draws of every i, and random bytes."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    tau = {2: 39, 3: 49, 5: 60}[level]
+    lo = 256 - tau
+    rng = np.random.default_rng(500 + level)
+    nb = 4
+    cases = []
+    for kind in range(8):
+        for _ in range(12):
+            s = rng.integers(0, 256, (nb, 136), dtype=np.uint8)
+            if kind == 1:                                  # heavy rejection
+                s = rng.integers(lo - 20, 256, (nb, 136)).astype(np.uint8)
+            elif kind == 2:                                # block 0 all rejected
+                s[0, 8:] = 255
+            elif kind == 3:                                # few distinct positions
+                s[:, :] = rng.choice([0, 1, 2, lo, lo + 1, lo + 2], (nb, 136)).astype(np.uint8)
+                s[0, :8] = rng.integers(0, 256, 8, dtype=np.uint8)
+            elif kind == 4:                                # b = i at every step
+                s[0, 8:8 + tau] = np.arange(lo, 256, dtype=np.uint8)
+            elif kind == 5:                                # draws of earlier i's
+                s[:, :] = rng.integers(lo, 256, (nb, 136)).astype(np.uint8)
+                s[0, :8] = rng.integers(0, 256, 8, dtype=np.uint8)
+            elif kind == 6:                                # rejections across the first chunk boundaries
+                s[0, 8:136] = np.where(rng.random(128) < 0.6, 255, s[0, 8:136]).astype(np.uint8)
+            elif kind == 7:                                # two blocks fully rejected
+                s[0, 8:] = 255
+                s[1, :] = 255
+            cases.append(s)
+    data = np.stack(cases)
+    n = data.shape[0]
+    out = torch.empty((n, 256), dtype=torch.int32, device="cuda")
+    dil.dil_test_sample_in_ball_stream(ctx.handle, level, n, dev(data), nb, out)
+    got = host(out)
+    for i in range(n):
+        want = _sib_reference(list(data[i]), tau)
+        assert np.array_equal(got[i], want), (i, i // 12)
+        assert int(np.abs(got[i]).sum()) == tau
