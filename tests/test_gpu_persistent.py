@@ -143,3 +143,18 @@ def test_cancel_running_launch(torch_cuda):
         (got,) = _persistent(torch, ctx, [small])
     for a, b in zip(got, _plain(torch, small)):
         assert np.array_equal(a, b)
+
+
+def test_empty_job_among_others(torch_cuda):
+    """A job with no tasks between two others: the launch signs the others
+    exactly as the plain form does (task indices skip the empty job)."""
+    from paper_2211_12265_gb300 import dil
+    a = _job_inputs(torch_cuda, 2, 120, 40)
+    c = _job_inputs(torch_cuda, 3, 70, 41, 0, 900)
+    empty = dict(level=5, n=0, sk=a["sk"][:0], msg=a["msg"][:0], off=a["off"][:1])
+    with dil.Context(0) as ctx:
+        got = _persistent(torch_cuda, ctx, [a, empty, c])
+    for j, g in ((a, got[0]), (c, got[2])):
+        for x, y in zip(g, _plain(torch_cuda, j)):
+            assert np.array_equal(x, y)
+    assert got[1][0].size == 0
