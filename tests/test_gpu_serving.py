@@ -16,7 +16,10 @@ def keys():
     return serving.make_keys((2, 3, 5), n_keys=64)
 
 
-def test_keyed_ops_match_plain(keys, orc):
+@pytest.mark.parametrize("sign_shape", [(2, 1), (8, 4), (4, 2)])
+def test_keyed_ops_match_plain(keys, orc, sign_shape):
+    """Keyed Sign / Verify equal the plain entry points; task groups of more
+    than one warp take mu and rho' from the one-warp prepass."""
     import torch
     from paper_2211_12265_gb300 import dil, workload as W
     for level in (2, 3, 5):
@@ -28,6 +31,7 @@ def test_keyed_ops_match_plain(keys, orc):
         msg, off = W.messages(lens, 40 + level)
         d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         with dil.Context(0) as ctx:
+            ctx.set_tuning(1, sign_shape[0], sign_shape[1], level)
             ks = dil.dil_keystore_create(ctx.handle, level, pk.shape[0], d(pk), d(sk))
             try:
                 sig_k = torch.empty((n, dil.SIZES[level][2]), dtype=torch.uint8, device="cuda")
