@@ -299,6 +299,14 @@ int dil_verify_host(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const 
  * strings (in, in_off as for messages) -> outlen bytes each (out: n x outlen). */
 int dil_test_shake(dil_ctx *ctx, int kind, size_t n, const uint8_t *in, const uint64_t *in_off,
                    uint8_t *out, size_t outlen, void *stream);
+/* SHAKE256 (rate 136) of n byte strings (in, in_off as for messages) -> the
+ * first 32 output bytes each (out: n x 32), computed the way Verify computes
+ * tr = H(pk) for Dilithium3/5: the hash rides in the spare instance of
+ * perms[i] sixteen-state permutations (one rate block absorbed before each)
+ * and, if unfinished, completes on the 25-lane form.  perms: n int32
+ * (device), any value >= 0; the result does not depend on it. */
+int dil_test_k16_rider(dil_ctx *ctx, size_t n, const uint8_t *in, const uint64_t *in_off, const int32_t *perms,
+                       uint8_t *out, void *stream);
 /* Keccak-f[1600] (FIPS 202; section 3.3 of arXiv 2211.12265 for the warp
  * form) of n states, each 25 little-endian 64-bit lanes, lane x + 5y at
  * index x + 5y (in, out: n x 25 uint64, device).  form selects the

@@ -115,20 +115,125 @@ __device__ __forceinline__ void keccak16_permute(uint32_t *kst) { keccak16_permu
 // tail_of(s) (the instance's nonce bytes followed by the SHAKE
 // domain/padding byte 0x1F), and the final padding bit at the last byte of
 // the rate.  Instances >= count get the same seed with tail 0 (their output is
-// never read).
+// never read); instances >= keep are left as they are.
 template <class Tail>
 __device__ __forceinline__ void keccak16_seed(uint32_t *kst, const uint32_t *seed, int seed_words, Tail tail_of,
-                                              int count, int rate, int lane) {
+                                              int count, int rate, int lane, int keep = K16_STATES) {
     const int s = lane >> 1, p = lane & 1;
     const uint32_t tail = s < count ? tail_of(s) : 0u;
+    if (s < keep) {
 #pragma unroll 1
-    for (int i = 0; i < 25; ++i) {
-        const int w = 2 * i + p;
-        uint32_t v = w < seed_words ? seed[w] : w == seed_words ? tail : 0u;
-        if (w == rate / 4 - 1) v ^= 0x80000000u;
-        kst[k16_slot(i, lane)] = v;
+        for (int i = 0; i < 25; ++i) {
+            const int w = 2 * i + p;
+            uint32_t v = w < seed_words ? seed[w] : w == seed_words ? tail : 0u;
+            if (w == rate / 4 - 1) v ^= 0x80000000u;
+            kst[k16_slot(i, lane)] = v;
+        }
     }
     __syncwarp();
 }
+
+// A SHAKE256 hash of `len` bytes of global memory (any alignment) that
+// rides in the last instance (15) of the sixteen-state batches of a sampler:
+// before each of the batch's permutations one 136-byte rate block of the
+// input (the last one padded) is absorbed into instance 15, so the hash
+// needs no permutation of its own.  Once the permutation after the final
+// block has run, the first 32 output bytes go to `out` (8-byte aligned
+// shared memory).  A hash longer than the batches' permutations is finished
+// on the 25-lane form (finish).  The samplers that carry it use instances
+// 0..14 only.  Block counts are 32-bit: an input of 2^31 blocks (292 GB)
+// would not fit in device memory.
+struct K16Rider {
+    static constexpr int SLOT = K16_STATES - 1;
+    static constexpr int KEEP = SLOT;   // instances a carrying sampler may seed
+    static constexpr int RATE = 136;
+    const uint8_t *src;
+    size_t len;
+    uint32_t out;   // shared-memory address
+    int next;       // next block to absorb; total + 1 once the output is taken
+    int total;      // blocks of the padded input
+
+    __device__ K16Rider(const uint8_t *src_, size_t len_, uint32_t *out_)
+        : src(src_), len(len_), out(smem_addr(out_)), next(0), total((int)(len_ / RATE) + 1) {}
+
+    // This lane's 8 input bytes of block blk (lane < 17), padded in the
+    // final block.
+    __device__ __forceinline__ uint64_t word(int blk, int lane) const {
+        const size_t off = (size_t)blk * RATE + 8 * lane;
+        const uint8_t *p = src + off;
+        uint64_t w = 0;
+        if (off + 8 <= len && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+            w = ((uint64_t)v.y << 32) | v.x;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (off + k < len) w |= (uint64_t)p[k] << (8 * k);
+        }
+        if (blk == total - 1) pad_word(w, (int)(len - (size_t)blk * RATE), RATE, lane);
+        return w;
+    }
+
+    // Absorbs the next block into instance SLOT (called by all 32 lanes right
+    // before a permutation).
+    __device__ __forceinline__ void before(uint32_t *kst, int lane) {
+        if (next >= total) return;
+        const int blk = next++;
+        if (lane < 25) {
+            const uint64_t w = lane < RATE / 8 ? word(blk, lane) : 0;
+            uint32_t *st = kst + k16_slot(lane, 2 * SLOT);
+            if (blk == 0) {
+                st[0] = (uint32_t)w;
+                st[1] = (uint32_t)(w >> 32);
+            } else {
+                st[0] ^= (uint32_t)w;
+                st[1] ^= (uint32_t)(w >> 32);
+            }
+        }
+        __syncwarp();
+    }
+
+    // Takes the output once the final block has been permuted (called by all
+    // 32 lanes right after a permutation).
+    __device__ __forceinline__ void after(const uint32_t *kst, int lane) {
+        if (next != total) return;
+        if (lane < 8)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(out + 4 * lane), "r"(kst[k16_word(SLOT, lane)]) : "memory");
+        next = total + 1;
+        __syncwarp();
+    }
+
+    // Completes an unfinished hash on the 25-lane form from instance SLOT's
+    // state (all 32 lanes; kst must still hold the batches' states).  Every
+    // before() is followed by a permutation and after(), so here either the
+    // output is taken (next > total) or the state is that after the
+    // permutation of block next - 1 (next < total).
+    __device__ __forceinline__ void finish(const uint32_t *kst, int lane) {
+        if (next > total) return;
+        uint32_t lo = 0, hi = 0;
+        if (next > 0 && lane < 25) {
+            lo = kst[k16_slot(lane, 2 * SLOT)];
+            hi = kst[k16_slot(lane, 2 * SLOT + 1)];
+        }
+#pragma unroll 1
+        for (; next < total; ++next) {
+            const uint64_t w = lane < RATE / 8 ? word(next, lane) : 0;
+            lo ^= (uint32_t)w;
+            hi ^= (uint32_t)(w >> 32);
+            keccak_f(lo, hi);
+        }
+        if (lane < 4)
+            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(out + 8 * lane), "r"(lo), "r"(hi) : "memory");
+        next = total + 1;
+        __syncwarp();
+    }
+};
+
+// The no-op rider of the samplers that carry none.
+struct K16NoRider {
+    static constexpr int KEEP = K16_STATES;
+    __device__ __forceinline__ void before(uint32_t *, int) {}
+    __device__ __forceinline__ void after(const uint32_t *, int) {}
+};
 
 }  // namespace dil

@@ -32,6 +32,26 @@ __global__ void k_test_shake(int n, int rate, const uint8_t *in, const uint64_t 
     }
 }
 
+// SHAKE256 of byte string `item` carried by a K16Rider through perms[item]
+// sixteen-state permutations (the other instances hold zero states), then
+// finished on the 25-lane form: the first 32 output bytes to out + 32 item.
+__global__ void k_test_k16_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms,
+                                 uint8_t *out) {
+    PRIM_PROLOGUE
+    for (int i = 0; i < 25; ++i) ws.k16[k16_slot(i, lane)] = 0u;
+    __syncwarp();
+    K16Rider rider(in + off[item], (size_t)(off[item + 1] - off[item]), reinterpret_cast<uint32_t *>(gs.tr));
+    const int np = perms[item];
+#pragma unroll 1
+    for (int p = 0; p < np; ++p) {
+        rider.before(ws.k16, lane);
+        keccak16_permute(ws.k16);
+        rider.after(ws.k16, lane);
+    }
+    rider.finish(ws.k16, lane);
+    out[(size_t)item * 32 + lane] = gs.tr[lane];
+}
+
 __global__ void k_test_ntt(int n, const int32_t *in, int32_t *out, int inverse) {
     PRIM_PROLOGUE
     int32_t r[8];
@@ -415,6 +435,10 @@ static cudaError_t launch_prim(Kern kern, int n, cudaStream_t s, Args... args) {
 cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t *off, uint8_t *out, int outlen,
                               cudaStream_t s) {
     return launch_prim(k_test_shake, n, s, kind == 128 ? 168 : 136, in, off, out, outlen);
+}
+cudaError_t launch_test_k16_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms, uint8_t *out,
+                                  cudaStream_t s) {
+    return launch_prim(k_test_k16_rider, n, s, in, off, perms, out);
 }
 cudaError_t launch_test_ntt(int n, const int32_t *in, int32_t *out, int inverse, cudaStream_t s) {
     return launch_prim(k_test_ntt, n, s, in, out, inverse);

@@ -189,16 +189,21 @@ __device__ __forceinline__ int share_lo(int g) { return g * M / P; }
 
 // A^_p (p = i l + j) for p in [lo, hi) into out + p N in index order: up to
 // sixteen sponges at a time while at least seven remain, six at a time while
-// at least three remain, then a pair or a single.
-template <int LEVEL>
-__device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out, WarpSmem &ws, int lane) {
+// at least three remain, then a pair or a single.  With a K16Rider the
+// sixteen-state batches take fifteen polynomials and carry the rider's hash
+// in the sixteenth instance; the hash is finished before the smaller forms
+// reuse the batches' shared memory.
+template <int LEVEL, class Rider>
+__device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out, WarpSmem &ws, int lane,
+                               Rider &rider) {
     constexpr int L = Lv<LEVEL>::L;
     int p = lo;
     while (hi - p >= 7) {
-        const int c = min(K16_STATES, hi - p);
-        expand_a_16<L>(rho, p, c, out + p * N, ws.k16, lane);
+        const int c = min(Rider::KEEP, hi - p);
+        expand_a_16<L>(rho, p, c, out + p * N, ws.k16, lane, rider);
         p += c;
     }
+    if constexpr (Rider::KEEP < K16_STATES) rider.finish(ws.k16, lane);
     while (hi - p >= 3) {
         const int c = min(K6_STATES, hi - p);
         expand_a_six<L>(rho, p, c, out + p * N, ws.kst, ws.kpi(), lane);
@@ -217,6 +222,13 @@ __device__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out,
         store_l2(out + p * N, a, lane);
     }
     __syncwarp();
+}
+
+template <int LEVEL>
+__device__ __forceinline__ void expand_a_range(const uint8_t *rho, int lo, int hi, int32_t *out, WarpSmem &ws,
+                                               int lane) {
+    K16NoRider none;
+    expand_a_range<LEVEL>(rho, lo, hi, out, ws, lane, none);
 }
 
 // Slot of nonce u's mask polynomial y (coefficient order) in the ring.
@@ -801,16 +813,23 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         ntt_fwd(r, ws.buf, zt, lane);
         store_l2(scratch + j * N, r, lane);
     }
-    // A^ = ExpandA(rho) into scratch after z^ (unless resident)
+    // A^ = ExpandA(rho) into scratch after z^ (unless resident).  A single
+    // warp with more than one sixteen-state batch of A^ carries H(pk) in the
+    // batches' spare instance.
     constexpr int KL = V::K * V::L;
-    if (!KEYED)
+    constexpr bool RIDE = P == 1 && !KEYED && KL > K16_STATES;
+    if constexpr (RIDE) {
+        K16Rider rider(pk, V::PK, reinterpret_cast<uint32_t *>(gs.tr));
+        expand_a_range<LEVEL>(gs.rho, 0, KL, scratch + V::L * N, ws, lane, rider);
+    } else if (!KEYED) {
         expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
+    }
     // mu = H(H(rho || t1) || M), on the last warp
     if (g == P - 1) {
         uint32_t lo = 0, hi = 0;
         if (KEYED) {
             gs.tr[lane] = __ldcg(tr + lane);
-        } else {
+        } else if (!RIDE) {
             absorb_concat(lo, hi, gs.tr, 0, pk, V::PK, 136, lane);
             squeeze_words(lo, hi, gs.tr, 4, lane);
         }

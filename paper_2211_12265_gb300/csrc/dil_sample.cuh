@@ -124,17 +124,20 @@ __device__ __forceinline__ void expand_a_six(const uint8_t *rho, int p0, int cou
     }
 }
 
-// Sixteen-instance ExpandA: polynomials p0 .. p0 + count - 1 (count <= 16),
-// written like expand_a_six.  The candidates of two instances are voted on at
-// once, one per half-warp (4 x 16 candidate slots for a block's 56).
-template <int L>
+// Sixteen-instance ExpandA: polynomials p0 .. p0 + count - 1 (count <=
+// Rider::KEEP), written like expand_a_six.  The candidates of two instances
+// are voted on at once, one per half-warp (4 x 16 candidate slots for a
+// block's 56).  `rider` may carry a hash in the last instance (K16Rider).
+template <int L, class Rider>
 __device__ __forceinline__ void expand_a_16(const uint8_t *rho, int p0, int count, int32_t *out, uint32_t *kst,
-                                            int lane) {
+                                            int lane, Rider &rider) {
     keccak16_seed(
         kst, reinterpret_cast<const uint32_t *>(rho), 8,
         [&](int s) { const int p = p0 + s; return (uint32_t)(p % L) | ((uint32_t)(p / L) << 8) | (0x1Fu << 16); },
-        count, 168, lane);
+        count, 168, lane, Rider::KEEP);
+    rider.before(kst, lane);
     keccak16_permute(kst);
+    rider.after(kst, lane);
     const int half = lane >> 4, hl = lane & 15;
     const uint32_t below = (1u << hl) - 1u;
     int mine = 0;   // lane s < count: coefficients accepted so far for instance s
@@ -164,9 +167,18 @@ __device__ __forceinline__ void expand_a_16(const uint8_t *rho, int p0, int coun
         }
         if (!__any_sync(FULL, lane < count && mine < N)) break;
         __syncwarp();
+        rider.before(kst, lane);
         keccak16_permute(kst);
+        rider.after(kst, lane);
     }
     __syncwarp();
+}
+
+template <int L>
+__device__ __forceinline__ void expand_a_16(const uint8_t *rho, int p0, int count, int32_t *out, uint32_t *kst,
+                                            int lane) {
+    K16NoRider none;
+    expand_a_16<L>(rho, p0, count, out, kst, lane, none);
 }
 
 // Sixteen-instance ExpandMask: y for nonces nonce0 .. nonce0 + count - 1

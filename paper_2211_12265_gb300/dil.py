@@ -63,6 +63,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_shake": [P, I, S, P, P, P, S, P],
                 "dil_test_ntt": [P, S, P, P, I, P],
                 "dil_test_keccak_f": [P, I, S, P, P, P],
+                "dil_test_k16_rider": [P, S, P, P, P, P, P],
                 "dil_test_t0_ntt": [P, I, I, S, P, P, P],
                 "dil_test_sample_in_ball_stream": [P, I, S, P, I, P, P],
                 "dil_test_expand_a": [P, I, S, P, P, P],
@@ -223,6 +224,11 @@ def dil_test_shake(ctx, kind, n, inp, in_off, out, outlen, stream=None):
 def dil_test_keccak_f(ctx, form, n, inp, out, stream=None):
     return _check(load().dil_test_keccak_f(ctx, int(form), n, _ptr(inp), _ptr(out), _stream(stream)),
                   "dil_test_keccak_f")
+
+
+def dil_test_k16_rider(ctx, n, inp, in_off, perms, out, stream=None):
+    return _check(load().dil_test_k16_rider(ctx, n, _ptr(inp), _ptr(in_off), _ptr(perms), _ptr(out),
+                                            _stream(stream)), "dil_test_k16_rider")
 
 
 def dil_test_sample_in_ball_stream(ctx, level, n, data, blocks, out, stream=None):

@@ -60,6 +60,38 @@ def test_shake_lengths(ctx, orc):
         assert got[5].tobytes() == (orc.shake128 if kind == 128 else orc.shake256)(msg[off[5]:off[6]].tobytes(), outlen)
 
 
+def test_k16_rider_hash(ctx, orc):
+    """The hash that rides in the spare sixteen-state instance (Verify's
+    tr = H(pk) for Dilithium3/5) against the oracle's SHAKE256 for every
+    way the ride can end: finished on the 25-lane form from the zero state
+    (0 permutations), part way, one block short, exactly at the final padded
+    block, and past it (later permutations must not touch the taken output);
+    lengths around the 136-byte rate, a whole number of blocks (pure padding
+    block), the three public-key sizes; each on an 8-byte-aligned and an
+    unaligned start (the two load paths).  One launch per case, so that each
+    string's start is chosen freely."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    rng = np.random.default_rng(7)
+    cases = []
+    for ln in (0, 1, 7, 8, 9, 135, 136, 137, 271, 272, 273, 1000, 1312, 1952, 2592):
+        total = ln // 136 + 1
+        for p in sorted({0, 1, max(total - 1, 0), total, total + 1, total + 3}):
+            cases += [(ln, p, 0), (ln, p, 3)]          # start mod 8
+    buf = rng.integers(0, 256, 4096, dtype=np.uint8)
+    d_buf = dev(buf)
+    out = torch.empty((len(cases), 32), dtype=torch.uint8, device="cuda")
+    for i, (ln, p, mis) in enumerate(cases):
+        start = 64 + mis
+        dil.dil_test_k16_rider(ctx.handle, 1, d_buf, dev(np.array([start, start + ln], dtype=np.uint64)),
+                               dev(np.array([p], dtype=np.int32)), out[i:i + 1])
+    got = host(out)
+    for i, (ln, p, mis) in enumerate(cases):
+        want = orc.shake256(buf[64 + mis:64 + mis + ln].tobytes(), 32)
+        assert got[i].tobytes() == want, (ln, p, mis)
+
+
 def test_ntt_forward_and_inverse(ctx, orc):
     import torch
     from gpu_util import dev, host
