@@ -314,12 +314,24 @@ __global__ void k_test_expand_s(int n, const uint8_t *rhop, int32_t *out) {
     using V = Lv<LEVEL>;
     stage_bytes(gs.rhop, rhop + (size_t)item * 64, 64, lane);
     __syncwarp();
+    int32_t *o = out + (size_t)item * (V::K + V::L) * N;
+    if (item % 3 == 2) {   // items 2 mod 3: all l + k sponges in one sixteen-state batch
+        expand_s_16<V::ETA>(gs.rhop, V::L + V::K, o, ws.k16, lane);
+        return;
+    }
+    int32_t a[8];
     for (int j = 0; j < V::L + V::K; ++j) {
-        expand_s_poly<V::ETA>(gs.rhop, j, ws.buf, ws.sq, lane);
-        int32_t a[8];
+        if (item % 3 == 1 && j + 1 < V::L + V::K) {   // items 1 mod 3: pairs, then a single tail
+            expand_s_pair<V::ETA>(gs.rhop, j, j + 1, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
+            read_buf_l0(a, ws.buf2, lane);
+            store_l0(o + (j + 1) * N, a, lane);
+        } else {               // items 0 mod 3: one sponge at a time
+            expand_s_poly<V::ETA>(gs.rhop, j, ws.buf, ws.sq, lane);
+        }
         read_buf_l0(a, ws.buf, lane);
         __syncwarp();
-        store_l0(out + ((size_t)item * (V::K + V::L) + j) * N, a, lane);
+        store_l0(o + j * N, a, lane);
+        if (item % 3 == 1 && j + 1 < V::L + V::K) ++j;
     }
 }
 

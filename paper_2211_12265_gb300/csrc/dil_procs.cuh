@@ -174,7 +174,8 @@ template <int LEVEL> struct Scratch {
     static constexpr int Z = W + V::K;
     static constexpr int ITR_POLYS = Z + V::L;
     static constexpr int SIGN_POLYS = PRE_POLYS + ITR_POLYS;
-    static constexpr int GEN_POLYS = V::L + V::K * V::L;      // s^1, A^
+    static constexpr int GEN_S = V::L + V::K * V::L;         // s1 and s2, sampled together (one-warp groups)
+    static constexpr int GEN_POLYS = GEN_S + V::L + V::K;     // s^1, A^, s1 || s2
     static constexpr int VERIFY_POLYS = V::L + V::K * V::L;   // z^, A^
     static constexpr int KEYED_VERIFY_POLYS = V::L;           // z^ (A^ is resident)
     // resident key: the Sign precomputation followed by NTT(t1 2^d)
@@ -371,10 +372,25 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
         gs.rhop[32 + lane] = gs.hb[64 + lane];
     }
     group_sync<P>(bar);
-    // s1: sample, pack into sk, NTT
+    using S = Scratch<LEVEL>;
+    int32_t *sraw = scratch + S::GEN_S * N;
+    if constexpr (P == 1) {
+        // s1 || s2 = ExpandS(rho'): all l + k sponges in one sixteen-state batch,
+        // then s1: pack into sk, NTT
+        expand_s_16<V::ETA>(gs.rhop, V::L + V::K, sraw, ws.k16, lane);
+#pragma unroll 1
+        for (int j = 0; j < V::L; ++j) {
+            load_l2(a, sraw + j * N, lane);
+            pack_seq<V::ETABITS>(sk + V::SK_S1 + j * V::POLYETA, a, V::ETA, -1, lane);
+            load_l0(r, sraw + j * N, lane);
+            ntt_fwd(r, ws.buf, zt, lane);
+            store_l2(scratch + j * N, r, lane);
+        }
+    }
+    // s1: sample, pack into sk, NTT (task groups of several warps)
     constexpr int U1 = Units<V::L, P>::SIZE;
 #pragma unroll 1
-    for (int j = U1 * g; j < V::L; j += U1 * P) {
+    for (int j = U1 * g; j < V::L && P > 1; j += U1 * P) {
         const bool two = U1 == 2 && j + 1 < V::L;
         if (two)
             expand_s_pair<V::ETA>(gs.rhop, j, j + 1, ws.buf, ws.buf2, ws.sq, ws.sq2, lane);
@@ -403,12 +419,17 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = reduce_q(acc[m]);
         ntt_inv(acc, ws.buf, izt, lane);
-        expand_s_poly<V::ETA>(gs.rhop, V::L + i, ws.buf, ws.sq, lane);
+        if constexpr (P == 1) {
+            load_l2(a, sraw + (V::L + i) * N, lane);
+            load_l0(r, sraw + (V::L + i) * N, lane);
+        } else {
+            expand_s_poly<V::ETA>(gs.rhop, V::L + i, ws.buf, ws.sq, lane);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) a[m] = ws.buf[8 * lane + m + 4 * (lane >> 2)];
+            for (int m = 0; m < 8; ++m) a[m] = ws.buf[8 * lane + m + 4 * (lane >> 2)];
+            read_buf_l0(r, ws.buf, lane);
+            __syncwarp();
+        }
         pack_seq<V::ETABITS>(sk + V::SK_S2 + i * V::POLYETA, a, V::ETA, -1, lane);
-        read_buf_l0(r, ws.buf, lane);
-        __syncwarp();
         int32_t t1[8], t0[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {

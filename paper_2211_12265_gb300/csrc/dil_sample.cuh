@@ -324,6 +324,55 @@ __device__ __forceinline__ void expand_s_pair(const uint8_t *rhop, int nonce0, i
     }
 }
 
+// Sixteen-instance ExpandS: polynomials with nonces 0 .. count - 1 (count <=
+// 16; s1 then s2), coefficient c of polynomial s to out[s N + c] (coefficient
+// order, global memory).  The candidates of two instances are voted on at
+// once, one per half-warp: 9 rounds of 16 bytes cover a block's 136.
+template <int ETA>
+__device__ __forceinline__ void expand_s_16(const uint8_t *rhop, int count, int32_t *out, uint32_t *kst,
+                                            int lane) {
+    keccak16_seed(
+        kst, reinterpret_cast<const uint32_t *>(rhop), 16, [](int s) { return (uint32_t)s | (0x1Fu << 16); },
+        count, 136, lane);
+    keccak16_permute(kst);
+    const int half = lane >> 4, hl = lane & 15;
+    const uint32_t below = (1u << hl) - 1u;
+    int mine = 0;   // lane s < count: coefficients accepted so far for instance s
+#pragma unroll 1
+    for (int blk = 0; blk < MAX_SQUEEZE_BLOCKS; ++blk) {
+#pragma unroll 1
+        for (int q = 0; 2 * q < count; ++q) {
+            const int s = 2 * q + half;
+            int c = __shfl_sync(FULL, mine, s);
+            const bool live = s < count && c < N;
+            if (!__any_sync(FULL, live)) continue;
+            int32_t *dst = out + s * N;
+#pragma unroll
+            for (int rnd = 0; rnd < 9; ++rnd) {
+                const int b = rnd * 16 + hl;
+                const bool valid = live && b < 136;
+                const uint32_t byte = valid ? (kst[k16_word(s, b >> 2)] >> (8 * (b & 3))) & 0xFFu : 0xFFu;
+                const uint32_t t0 = byte & 15u, t1 = byte >> 4;
+                const bool a0 = valid && (ETA == 2 ? t0 < 15u : t0 < 9u);
+                const bool a1 = valid && (ETA == 2 ? t1 < 15u : t1 < 9u);
+                const uint32_t m0 = __ballot_sync(FULL, a0) >> (16 * half) & 0xFFFFu;
+                const uint32_t m1 = __ballot_sync(FULL, a1) >> (16 * half) & 0xFFFFu;
+                const int pos0 = c + __popc(m0 & below) + __popc(m1 & below);
+                const int pos1 = pos0 + (a0 ? 1 : 0);
+                if (a0 && pos0 < N) dst[pos0] = (ETA == 2) ? 2 - (int32_t)(t0 % 5u) : 4 - (int32_t)t0;
+                if (a1 && pos1 < N) dst[pos1] = (ETA == 2) ? 2 - (int32_t)(t1 % 5u) : 4 - (int32_t)t1;
+                c += __popc(m0) + __popc(m1);
+            }
+            const int c_new = __shfl_sync(FULL, c, (lane & 1) << 4);
+            if ((lane >> 1) == q) mine = c_new;
+        }
+        if (!__any_sync(FULL, lane < count && mine < N)) break;
+        __syncwarp();
+        keccak16_permute(kst);
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- ExpandMask
 // y = gamma1 - t for consecutive ZBITS-bit fields t of SHAKE256(rho' || nonce).
 // Results are in layout L0.  sq holds 5 x 136 squeezed bytes (+ slack).
