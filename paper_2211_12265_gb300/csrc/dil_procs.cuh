@@ -174,8 +174,8 @@ template <int LEVEL> struct Scratch {
     static constexpr int Z = W + V::K;
     static constexpr int ITR_POLYS = Z + V::L;
     static constexpr int SIGN_POLYS = PRE_POLYS + ITR_POLYS;
-    static constexpr int GEN_S = V::L + V::K * V::L;         // s1 and s2, sampled together (one-warp groups)
-    static constexpr int GEN_POLYS = GEN_S + V::L + V::K;     // s^1, A^, s1 || s2
+    static constexpr int GEN_S = V::L + V::K * V::L;         // s1 || s2, coefficient order (one-warp groups)
+    static constexpr int GEN_POLYS = GEN_S + V::L + V::K;     // s^1 | A^ | s1 || s2
     static constexpr int VERIFY_POLYS = V::L + V::K * V::L;   // z^, A^
     static constexpr int KEYED_VERIFY_POLYS = V::L;           // z^ (A^ is resident)
     // resident key: the Sign precomputation followed by NTT(t1 2^d)
