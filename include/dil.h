@@ -307,6 +307,15 @@ int dil_test_shake(dil_ctx *ctx, int kind, size_t n, const uint8_t *in, const ui
  * (device), any value >= 0; the result does not depend on it. */
 int dil_test_k16_rider(dil_ctx *ctx, size_t n, const uint8_t *in, const uint64_t *in_off, const int32_t *perms,
                        uint8_t *out, void *stream);
+/* As dil_test_k16_rider, for the hash KeyGen computes as tr = H(pk) while
+ * the rows of t1 are still being packed (Dilithium3/5): before permutation p
+ * only the first min(len, p * step[i]) bytes count as written (the hash
+ * advances only on permutations whose next block is complete), and the
+ * riding instance is overwritten between permutations, as the samplers'
+ * shared memory is.  step: n int32 (device, negative counts as 0).  The
+ * result depends on neither perms nor step. */
+int dil_test_k16_chain_rider(dil_ctx *ctx, size_t n, const uint8_t *in, const uint64_t *in_off,
+                             const int32_t *perms, const int32_t *step, uint8_t *out, void *stream);
 /* Keccak-f[1600] (FIPS 202; section 3.3 of arXiv 2211.12265 for the warp
  * form) of n states, each 25 little-endian 64-bit lanes, lane x + 5y at
  * index x + 5y (in, out: n x 25 uint64, device).  form selects the

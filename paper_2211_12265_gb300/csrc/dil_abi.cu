@@ -729,6 +729,15 @@ int dil_test_k16_rider(dil_ctx *c, size_t n, const uint8_t *in, const uint64_t *
     return status_of(dil::launch_test_k16_rider((int)n, in, in_off, perms, out, (cudaStream_t)stream));
 }
 
+int dil_test_k16_chain_rider(dil_ctx *c, size_t n, const uint8_t *in, const uint64_t *in_off, const int32_t *perms,
+                             const int32_t *step, uint8_t *out, void *stream) {
+    TEST_PROLOGUE(c)
+    if (n > (size_t)INT32_MAX) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!in_off || !perms || !step || !out) return DIL_EINVAL;
+    return status_of(dil::launch_test_k16_chain_rider((int)n, in, in_off, perms, step, out, (cudaStream_t)stream));
+}
+
 int dil_test_keccak_f(dil_ctx *c, int form, size_t n, const uint64_t *in, uint64_t *out, void *stream) {
     TEST_PROLOGUE(c)
     if ((form != 1 && form != 2 && form != 6 && form != 16) || n > (size_t)INT32_MAX) return DIL_EINVAL;

@@ -133,6 +133,26 @@ __device__ __forceinline__ void keccak16_seed(uint32_t *kst, const uint32_t *see
     __syncwarp();
 }
 
+// Lane `lane` (< 17)'s 8 bytes of 136-byte block blk of a `len`-byte SHAKE256
+// input at src (global memory, any alignment), padded in the final block
+// (total = len / 136 + 1 blocks).  Plain loads: bytes the same warp wrote
+// earlier in the kernel are seen.
+__device__ __forceinline__ uint64_t rider_word(const uint8_t *src, size_t len, int total, int blk, int lane) {
+    const size_t off = (size_t)blk * 136 + 8 * lane;
+    const uint8_t *p = src + off;
+    uint64_t w = 0;
+    if (off + 8 <= len && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        w = ((uint64_t)v.y << 32) | v.x;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (off + k < len) w |= (uint64_t)p[k] << (8 * k);
+    }
+    if (blk == total - 1) pad_word(w, (int)(len - (size_t)blk * 136), 136, lane);
+    return w;
+}
+
 // A SHAKE256 hash of `len` bytes of global memory (any alignment) that
 // rides in the last instance (15) of the sixteen-state batches of a sampler:
 // before each of the batch's permutations one 136-byte rate block of the
@@ -156,23 +176,7 @@ struct K16Rider {
     __device__ K16Rider(const uint8_t *src_, size_t len_, uint32_t *out_)
         : src(src_), len(len_), out(smem_addr(out_)), next(0), total((int)(len_ / RATE) + 1) {}
 
-    // This lane's 8 input bytes of block blk (lane < 17), padded in the
-    // final block.
-    __device__ __forceinline__ uint64_t word(int blk, int lane) const {
-        const size_t off = (size_t)blk * RATE + 8 * lane;
-        const uint8_t *p = src + off;
-        uint64_t w = 0;
-        if (off + 8 <= len && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(p);
-            w = ((uint64_t)v.y << 32) | v.x;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (off + k < len) w |= (uint64_t)p[k] << (8 * k);
-        }
-        if (blk == total - 1) pad_word(w, (int)(len - (size_t)blk * RATE), RATE, lane);
-        return w;
-    }
+    __device__ __forceinline__ uint64_t word(int blk, int lane) const { return rider_word(src, len, total, blk, lane); }
 
     // Absorbs the next block into instance SLOT (called by all 32 lanes right
     // before a permutation).
@@ -218,6 +222,84 @@ struct K16Rider {
 #pragma unroll 1
         for (; next < total; ++next) {
             const uint64_t w = lane < RATE / 8 ? word(next, lane) : 0;
+            lo ^= (uint32_t)w;
+            hi ^= (uint32_t)(w >> 32);
+            keccak_f(lo, hi);
+        }
+        if (lane < 4)
+            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(out + 8 * lane), "r"(lo), "r"(hi) : "memory");
+        next = total + 1;
+        __syncwarp();
+    }
+};
+
+// A SHAKE256 hash that rides like K16Rider over an input that is still being
+// written (KeyGen's H(pk) while the rows of t are packed): a permutation
+// advances it only when the next block's bytes exist (set_ready), and between
+// such permutations its state lives in shared memory (`save`, 25 x 8 bytes,
+// 8-byte aligned), so instance 15 may be overwritten in between (the other
+// instances' permutations, buffers in the same shared-memory union).  When
+// the final block has been permuted the first 32 output bytes go to `out`;
+// finish() completes the hash on the 25-lane form and must only be called
+// once all `len` bytes are written.
+struct K16ChainRider {
+    static constexpr int SLOT = K16_STATES - 1;
+    static constexpr int KEEP = SLOT;
+    static constexpr int RATE = 136;
+    const uint8_t *src;
+    size_t len;
+    uint32_t save, out;   // shared-memory addresses
+    int next;             // next block to absorb; total + 1 once the output is taken
+    int total;            // blocks of the padded input
+    int avail;            // blocks whose bytes exist
+    bool absorbed;        // the current permutation advances the hash
+
+    __device__ K16ChainRider(const uint8_t *src_, size_t len_, uint32_t *save_, uint32_t *out_)
+        : src(src_), len(len_), save(smem_addr(save_)), out(smem_addr(out_)), next(0),
+          total((int)(len_ / RATE) + 1), avail(0), absorbed(false) {}
+
+    // The first `bytes` bytes of the input are written (and visible to the warp).
+    __device__ __forceinline__ void set_ready(size_t bytes) {
+        avail = bytes >= len ? total : (int)(bytes / RATE);
+    }
+
+    __device__ __forceinline__ void before(uint32_t *kst, int lane) {
+        absorbed = next < avail;
+        if (!absorbed) return;
+        if (lane < 25) {
+            uint32_t lo = 0, hi = 0;
+            if (next > 0) asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(save + 8 * lane));
+            const uint64_t w = lane < RATE / 8 ? rider_word(src, len, total, next, lane) : 0;
+            uint32_t *st = kst + k16_slot(lane, 2 * SLOT);
+            st[0] = lo ^ (uint32_t)w;
+            st[1] = hi ^ (uint32_t)(w >> 32);
+        }
+        ++next;
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ void after(const uint32_t *kst, int lane) {
+        if (!absorbed) return;
+        absorbed = false;
+        if (lane < 25) {
+            const uint32_t lo = kst[k16_slot(lane, 2 * SLOT)], hi = kst[k16_slot(lane, 2 * SLOT + 1)];
+            if (next < total)
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(save + 8 * lane), "r"(lo), "r"(hi) : "memory");
+            else if (lane < 4)
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(out + 8 * lane), "r"(lo), "r"(hi) : "memory");
+        }
+        if (next == total) next = total + 1;
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ void finish(int lane) {
+        if (next > total) return;
+        uint32_t lo = 0, hi = 0;
+        if (next > 0 && lane < 25)
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(save + 8 * lane));
+#pragma unroll 1
+        for (; next < total; ++next) {
+            const uint64_t w = lane < RATE / 8 ? rider_word(src, len, total, next, lane) : 0;
             lo ^= (uint32_t)w;
             hi ^= (uint32_t)(w >> 32);
             keccak_f(lo, hi);

@@ -57,6 +57,8 @@ cudaError_t launch_test_ntt(int n, const int32_t *in, int32_t *out, int inverse,
 cudaError_t launch_test_keccak_f(int form, int states, const uint64_t *in, uint64_t *out, cudaStream_t s);
 cudaError_t launch_test_k16_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms, uint8_t *out,
                                   cudaStream_t s);
+cudaError_t launch_test_k16_chain_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms,
+                                        const int32_t *step, uint8_t *out, cudaStream_t s);
 // variant 0..3 of the t^0 = NTT(t0) breakdown; tmp: n k 256 int32 (variants 0, 1)
 cudaError_t launch_test_t0_ntt(int level, int variant, int n, const uint8_t *sk, int32_t *tmp, int32_t *out,
                                cudaStream_t s);

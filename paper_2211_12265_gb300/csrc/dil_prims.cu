@@ -52,6 +52,37 @@ __global__ void k_test_k16_rider(int n, const uint8_t *in, const uint64_t *off, 
     out[(size_t)item * 32 + lane] = gs.tr[lane];
 }
 
+// SHAKE256 of byte string `item` carried by a K16ChainRider through
+// perms[item] sixteen-state permutations; before permutation p the first
+// min(len, p * step[item]) bytes count as written, and after every
+// permutation instance 15 is overwritten (as the samplers' shared-memory
+// union does), so only the saved state may carry the hash.  Then finished on
+// the 25-lane form: the first 32 output bytes to out + 32 item.
+__global__ void k_test_k16_chain_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms,
+                                       const int32_t *step, uint8_t *out) {
+    PRIM_PROLOGUE
+    for (int i = 0; i < 25; ++i) ws.k16[k16_slot(i, lane)] = 0u;
+    __syncwarp();
+    const size_t len = (size_t)(off[item + 1] - off[item]);
+    K16ChainRider rider(in + off[item], len, reinterpret_cast<uint32_t *>(gs.hb), reinterpret_cast<uint32_t *>(gs.tr));
+    const int np = perms[item];
+    const size_t st = (size_t)max(step[item], 0);
+#pragma unroll 1
+    for (int p = 0; p < np; ++p) {
+        rider.set_ready(min(len, (size_t)p * st));
+        rider.before(ws.k16, lane);
+        keccak16_permute(ws.k16);
+        rider.after(ws.k16, lane);
+        if (lane < 25) {
+            ws.k16[k16_slot(lane, 30)] ^= 0x9E3779B9u * (p + 1);
+            ws.k16[k16_slot(lane, 31)] ^= 0x7F4A7C15u * (p + 1);
+        }
+        __syncwarp();
+    }
+    rider.finish(lane);
+    out[(size_t)item * 32 + lane] = gs.tr[lane];
+}
+
 __global__ void k_test_ntt(int n, const int32_t *in, int32_t *out, int inverse) {
     PRIM_PROLOGUE
     int32_t r[8];
@@ -451,6 +482,10 @@ cudaError_t launch_test_shake(int kind, int n, const uint8_t *in, const uint64_t
 cudaError_t launch_test_k16_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms, uint8_t *out,
                                   cudaStream_t s) {
     return launch_prim(k_test_k16_rider, n, s, in, off, perms, out);
+}
+cudaError_t launch_test_k16_chain_rider(int n, const uint8_t *in, const uint64_t *off, const int32_t *perms,
+                                        const int32_t *step, uint8_t *out, cudaStream_t s) {
+    return launch_prim(k_test_k16_chain_rider, n, s, in, off, perms, step, out);
 }
 cudaError_t launch_test_ntt(int n, const int32_t *in, int32_t *out, int inverse, cudaStream_t s) {
     return launch_prim(k_test_ntt, n, s, in, out, inverse);

@@ -408,13 +408,8 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
             store_l2(scratch + jj * N, r, lane);
         }
     }
-    // A^ = ExpandA(rho) into scratch after s^1
-    constexpr int KL = V::K * V::L;
-    expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
-    group_sync<P>(bar);
-    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t)
-#pragma unroll 1
-    for (int i = g; i < V::K; i += P) {
+    // t = INTT(A^ o s^1) + s2; (t1, t0) = Power2Round(t), row i into pk and sk
+    auto row = [&](int i) {
         accumulate_row(acc, scratch + (V::L + i * V::L) * N, V::L, scratch, lane);
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = reduce_q(acc[m]);
@@ -442,16 +437,43 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
         pack_seq<10>(pk + 32 + i * V::POLYT1, t1, 0, 1, lane);
         l0_to_seq(t0, ws.buf, lane);
         pack_seq<D>(sk + V::SK_T0 + i * V::POLYT0, t0, 1 << (D - 1), -1, lane);
-    }
-    __threadfence_block();
-    group_sync<P>(bar);
-    // tr = H(rho || t1)
-    if (g == 0) {
-        uint32_t lo = 0, hi = 0;
-        absorb_concat(lo, hi, gs.hb, 0, pk, V::PK, 136, lane);
-        if (lane < 4) {
+    };
+    constexpr int KL = V::K * V::L;
+    if constexpr (P == 1 && KL > K16_STATES) {
+        // A^ in sixteen-state batches of whole rows (R l <= 15 polynomials), the
+        // batch's rows of t computed before the next batch, and tr = H(rho || t1)
+        // riding in the batches' spare instance as far as pk is written.
+        constexpr int R = (K16_STATES - 1) / V::L;
+        K16ChainRider rider(pk, V::PK, reinterpret_cast<uint32_t *>(gs.hb), reinterpret_cast<uint32_t *>(gs.tr));
+        rider.set_ready(32);
+#pragma unroll 1
+        for (int i0 = 0; i0 < V::K; i0 += R) {
+            const int rows = min(R, V::K - i0);
+            expand_a_16<V::L>(gs.rho, i0 * V::L, rows * V::L, scratch + (V::L + i0 * V::L) * N, ws.k16, lane,
+                              rider);
+#pragma unroll 1
+            for (int i = i0; i < i0 + rows; ++i) row(i);
+            __syncwarp();
+            rider.set_ready(32 + (size_t)(i0 + rows) * V::POLYT1);
+        }
+        rider.finish(lane);
+        sk[64 + lane] = gs.tr[lane];
+    } else {
+        // A^ = ExpandA(rho) into scratch after s^1, then the rows of t
+        expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
+        group_sync<P>(bar);
+#pragma unroll 1
+        for (int i = g; i < V::K; i += P) row(i);
+        __threadfence_block();
+        group_sync<P>(bar);
+        // tr = H(rho || t1)
+        if (g == 0) {
+            uint32_t lo = 0, hi = 0;
+            absorb_concat(lo, hi, gs.hb, 0, pk, V::PK, 136, lane);
+            if (lane < 4) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sk[64 + 8 * lane + q] = (uint8_t)((q < 4 ? lo : hi) >> (8 * (q & 3)));
+                for (int q = 0; q < 8; ++q) sk[64 + 8 * lane + q] = (uint8_t)((q < 4 ? lo : hi) >> (8 * (q & 3)));
+            }
         }
     }
 }

@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_ntt": [P, S, P, P, I, P],
                 "dil_test_keccak_f": [P, I, S, P, P, P],
                 "dil_test_k16_rider": [P, S, P, P, P, P, P],
+                "dil_test_k16_chain_rider": [P, S, P, P, P, P, P, P],
                 "dil_test_t0_ntt": [P, I, I, S, P, P, P],
                 "dil_test_sample_in_ball_stream": [P, I, S, P, I, P, P],
                 "dil_test_expand_a": [P, I, S, P, P, P],
@@ -229,6 +230,11 @@ def dil_test_keccak_f(ctx, form, n, inp, out, stream=None):
 def dil_test_k16_rider(ctx, n, inp, in_off, perms, out, stream=None):
     return _check(load().dil_test_k16_rider(ctx, n, _ptr(inp), _ptr(in_off), _ptr(perms), _ptr(out),
                                             _stream(stream)), "dil_test_k16_rider")
+
+
+def dil_test_k16_chain_rider(ctx, n, inp, in_off, perms, step, out, stream=None):
+    return _check(load().dil_test_k16_chain_rider(ctx, n, _ptr(inp), _ptr(in_off), _ptr(perms), _ptr(step), _ptr(out),
+                                                  _stream(stream)), "dil_test_k16_chain_rider")
 
 
 def dil_test_sample_in_ball_stream(ctx, level, n, data, blocks, out, stream=None):

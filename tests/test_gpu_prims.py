@@ -92,6 +92,37 @@ def test_k16_rider_hash(ctx, orc):
         assert got[i].tobytes() == want, (ln, p, mis)
 
 
+def test_k16_chain_rider_hash(ctx, orc):
+    """The hash KeyGen carries while pk is being written (tr = H(pk) for
+    Dilithium3/5) against the oracle's SHAKE256: input made available in
+    steps of 0 (nothing until the end), less than, exactly and more than one
+    136-byte block, a t1 row (320 bytes) and all at once; no permutation,
+    fewer than the blocks, and more; the riding instance overwritten between
+    permutations; strings at assorted alignments (one launch)."""
+    import torch
+    from gpu_util import dev, host
+    from paper_2211_12265_gb300 import dil
+    rng = np.random.default_rng(8)
+    lens, perms, steps = [], [], []
+    for ln in (0, 1, 135, 136, 137, 1000, 1312, 1952, 2592):
+        total = ln // 136 + 1
+        for st in (0, 50, 136, 137, 320, 5000):
+            for p in sorted({0, 3, total, total + 5, 4 * total}):
+                lens.append(ln)
+                steps.append(st)
+                perms.append(p)
+    off = np.zeros(len(lens) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    buf = rng.integers(0, 256, int(off[-1]) + 8, dtype=np.uint8)
+    out = torch.empty((len(lens), 32), dtype=torch.uint8, device="cuda")
+    dil.dil_test_k16_chain_rider(ctx.handle, len(lens), dev(buf), dev(off), dev(np.array(perms, dtype=np.int32)),
+                                 dev(np.array(steps, dtype=np.int32)), out)
+    got = host(out)
+    for i in range(len(lens)):
+        want = orc.shake256(buf[off[i]:off[i + 1]].tobytes(), 32)
+        assert got[i].tobytes() == want, (lens[i], steps[i], perms[i])
+
+
 def test_ntt_forward_and_inverse(ctx, orc):
     import torch
     from gpu_util import dev, host
