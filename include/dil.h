@@ -134,7 +134,9 @@ typedef struct {
     const uint64_t *msg_off; /* n + 1 offsets (device) */
     uint8_t *sig;            /* n x SIG (device) */
     int32_t *task_status;    /* n (device, nullable): DIL_OK, DIL_EITER, DIL_EINVAL
-                                (decreasing offsets) or DIL_ECANCELED */
+                                (decreasing offsets), DIL_ECANCELED, or DIL_ETIMEOUT
+                                when a bounded device wait on this task ran out
+                                (then the signature is zeroed and iterations 0) */
     int32_t *iterations;     /* n (device, nullable): loop repetitions */
 } dil_sign_job;
 
@@ -155,8 +157,9 @@ int dil_set_persistent_tuning(dil_ctx *ctx, int warps_per_cta, int warps_per_tas
                               int speculation);
 
 /* Synchronises `stream` and returns DIL_OK, DIL_ETIMEOUT when a bounded
- * device-side wait of the last persistent launch on this context ran out, or
- * DIL_ECANCELED when that launch was canceled. */
+ * device-side wait of the last persistent launch on this context ran out (the
+ * tasks it concerned report DIL_ETIMEOUT; every other task's output is
+ * normal), or DIL_ECANCELED when that launch was canceled. */
 int dil_persistent_status(dil_ctx *ctx, void *stream);
 
 /* Cancels the persistent launch of this context that is running: sets its
@@ -358,6 +361,14 @@ int dil_test_sample_in_ball_stream(dil_ctx *ctx, int level, size_t n, const uint
  * MakeHint(z, r), UseHint(h, r). */
 int dil_test_rounding(dil_ctx *ctx, int level, size_t n, const int32_t *r, const int32_t *z,
                       const uint8_t *h, int32_t *out, void *stream);
+
+/* Failure-detection hook: the number of polls after which each bounded wait
+ * of later persistent launches on this context (the commit lock, an owner
+ * waiting for its helpers) gives up, 1..4194304; 0 restores the default
+ * (4194304, about half a second).  A low limit makes the real waits run out
+ * under ordinary contention, so tests can check the per-task DIL_ETIMEOUT
+ * path.  DIL_EINVAL outside that range. */
+int dil_test_set_spin_limit(dil_ctx *ctx, int limit);
 
 /* Failure-detection hook: runs the persistent scheduler's bounded device wait
  * (poll until a flag reads 0, at most `limit` polls of ~128 ns) on a flag set

@@ -34,6 +34,8 @@ struct dil_ctx {
     dil::PersistJobs gjobs{};
     dil::PersistTuning gtune;
     int gmax_iter = -1;
+    int spin_limit = 0;       // polls per bounded device wait (0 = PERSIST_SPIN_LIMIT); tests lower it
+    int gspin_limit = -1;
     void *gws = nullptr;
     // host-form pipeline: extra streams and the fork / join events
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
@@ -128,6 +130,7 @@ const char *dil_status_string(int status) {
         case DIL_ECUDA: return "CUDA error";
         case DIL_ETIMEOUT: return "device wait timed out";
         case DIL_EITER: return "sign repetition cap reached";
+        case DIL_ECANCELED: return "canceled";
     }
     return "unknown status";
 }
@@ -336,7 +339,7 @@ int dil_sign_persistent(dil_ctx *c, int njobs, const dil_sign_job *jobs, void *s
     }
     const int max_iter = c->max_iter;
     if (!c->gexec || !same_jobs(J, c->gjobs) || !same_tune(c->ptune, c->gtune) || max_iter != c->gmax_iter ||
-        c->gws != c->pws) {
+        c->spin_limit != c->gspin_limit || c->gws != c->pws) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
@@ -347,7 +350,8 @@ int dil_sign_persistent(dil_ctx *c, int njobs, const dil_sign_job *jobs, void *s
         if (dil::persist_workspace_bytes(J, c->ptune, c->device) == 0) return DIL_ECUDA;
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return DIL_ECUDA;
-        cudaError_t e = dil::launch_sign_persist(J, c->pws, c->ptune, max_iter, c->device, c->cap_stream);
+        cudaError_t e = dil::launch_sign_persist(J, c->pws, c->ptune, max_iter, c->spin_limit, c->device,
+                                                 c->cap_stream);
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -363,6 +367,7 @@ int dil_sign_persistent(dil_ctx *c, int njobs, const dil_sign_job *jobs, void *s
         c->gjobs = J;
         c->gtune = c->ptune;
         c->gmax_iter = max_iter;
+        c->gspin_limit = c->spin_limit;
         c->gws = c->pws;
     }
     return cudaGraphLaunch(c->gexec, (cudaStream_t)stream) == cudaSuccess ? DIL_OK : DIL_ECUDA;
@@ -811,6 +816,13 @@ int dil_test_bounded_wait(dil_ctx *c, int flag_value, int limit, int *result) {
     TEST_PROLOGUE(c)
     if (!result || limit < 1 || limit > (1 << 24)) return DIL_EINVAL;
     return status_of(dil::test_bounded_wait(flag_value, limit, result));
+}
+
+int dil_test_set_spin_limit(dil_ctx *c, int limit) {
+    TEST_PROLOGUE(c)
+    if (limit < 0 || limit > dil::PERSIST_SPIN_LIMIT) return DIL_EINVAL;
+    c->spin_limit = limit;
+    return DIL_OK;
 }
 
 int dil_test_issue_rate(dil_ctx *c, int op, double *thread_ops_per_sm_clk) {

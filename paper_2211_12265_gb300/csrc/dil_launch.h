@@ -33,6 +33,9 @@ cudaError_t launch_sign(int level, int n, const uint8_t *sk, const uint8_t *msg,
                         int warps, int p, cudaStream_t s);
 cudaError_t launch_verify(int level, int n, const uint8_t *pk, const uint8_t *msg, const uint64_t *off,
                           const uint8_t *sig, uint8_t *ok, int32_t *scratch, int warps, int p, cudaStream_t s);
+// Loads the one-warp-per-task Sign kernel of `level` and runs it once on no
+// tasks (its code and local-memory reservation are in place afterwards).
+cudaError_t warm_sign(int level, int warps, int p, cudaStream_t s);
 
 // resident keys: per-key polynomials (A^, s^1, s^2, t^0, NTT(t1 2^d)) and
 // per-task scratch of a keyed Sign (y, y^, w, z)
@@ -98,7 +101,8 @@ struct PersistTask {
     int committed_r;  // repetition whose signature is in the output
     int lock;         // commit lock
     int helpers;      // helper groups reading this task's precomputation
-    int pad[3];
+    int fail;         // a bounded wait on this task ran out (zeroed before each launch)
+    int pad[2];
 };
 // Queue header (device memory, zeroed before each launch).
 struct PersistQueue {
@@ -116,9 +120,12 @@ struct PersistTuning {
 };
 // Device bytes a persistent launch needs for `total` tasks of the given levels.
 size_t persist_workspace_bytes(const PersistJobs &J, const PersistTuning &t, int device);
-// Enqueues (memsets + kernel) on s; ws must hold persist_workspace_bytes.
+// Polls of a bounded device wait before it gives up (the default of a launch).
+constexpr int PERSIST_SPIN_LIMIT = 1 << 22;
+// Enqueues (memsets, kernel, finalize kernel) on s; ws must hold
+// persist_workspace_bytes.  spin_limit: polls per bounded wait (1..PERSIST_SPIN_LIMIT).
 cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTuning &t, int max_iter_override,
-                                int device, cudaStream_t s);
+                                int spin_limit, int device, cudaStream_t s);
 // Reads the device error word of the last launch on ws (synchronous).
 int persist_error(void *ws);
 cudaError_t persist_cancel(void *ws, cudaStream_t s);

@@ -16,9 +16,15 @@
 // r is skipped only when it exceeds an accepted one).
 //
 // Waits (commit lock, an owner waiting for its helpers before reusing its
-// slot) spin at most PERSIST_SPIN_LIMIT times; then the kernel records
-// DIL_ETIMEOUT in the queue's error word and continues.  The holders of these
-// waits never wait on anything themselves, so the limit is a safety net only.
+// slot) poll at most spin_limit times (PERSIST_SPIN_LIMIT unless a test lowers
+// it); then the kernel records DIL_ETIMEOUT in the queue's error word, marks
+// the task failed and continues.  Workers draw no further repetitions of a
+// failed task and write none of its results; a finalize kernel that runs
+// after the grid gives every failed task status DIL_ETIMEOUT, 0 repetitions
+// and a zeroed signature, so each task of a launch ends with a defined
+// output even though late writers (a helper still running when its owner's
+// wait gave up) may have touched it.  The holders of these waits never wait
+// on anything themselves, so the limit is a safety net only.
 #include <climits>
 #include <cstddef>
 
@@ -27,7 +33,6 @@
 
 namespace dil {
 
-constexpr int PERSIST_SPIN_LIMIT = 1 << 22;
 constexpr int PERSIST_META_POLYS = 1;   // mu (64 B) and rho' (64 B) of a slot's task
 
 __device__ __forceinline__ int ld_l2(const int *p) { return __ldcg(p); }
@@ -68,7 +73,14 @@ struct PersistCtx {
     int slots;
     int max_iter_override;
     int spec;
+    int spin_limit;
 };
+
+// A bounded wait on task tk ran out: record it launch-wide and on the task.
+__device__ __forceinline__ void wait_failed(const PersistCtx &pc, PersistTask &tk) {
+    atomicExch(&tk.fail, 1);
+    atomicExch(&pc.q->error, DIL_ETIMEOUT);
+}
 
 // Writes the signature of repetition r for task t if r beats the committed one.
 template <int LEVEL, int P>
@@ -78,16 +90,17 @@ __device__ void commit(const PersistCtx &pc, PersistTask &tk, int r, const Persi
     if (leader) {
         atomicMin(&tk.best_r, r);
         int acquired = 0;
-        for (int i = 0; i < PERSIST_SPIN_LIMIT; ++i) {
+        for (int i = 0; i < pc.spin_limit; ++i) {
             if (atomicCAS(&tk.lock, 0, 1) == 0) {
                 acquired = 1;
                 break;
             }
             __nanosleep(64);
         }
-        if (!acquired) atomicExch(&pc.q->error, DIL_ETIMEOUT);
+        if (!acquired) wait_failed(pc, tk);
         __threadfence();
-        const int win = acquired && r < atomicOr(&tk.committed_r, 0);
+        // a failed task's output is the finalize kernel's to write
+        const int win = acquired && r < atomicOr(&tk.committed_r, 0) && !atomicOr(&tk.fail, 0);
         gs.claim2 = acquired ? (win ? 2 : 1) : 0;
     }
     group_sync<P>(bar);
@@ -136,8 +149,8 @@ __device__ void run_repetitions(const PersistCtx &pc, PersistTask &tk, const Per
             }
             const int r = next++;
             const int best = atomicOr(&tk.best_r, 0);
-            const int canceled = ld_l2(&pc.q->cancel);
-            gs.claim2 = (!canceled && r < cap && r < best) ? r : -1;
+            const int stop = ld_l2(&pc.q->cancel) || ld_l2(&tk.fail);
+            gs.claim2 = (!stop && r < cap && r < best) ? r : -1;
         }
         group_sync<P>(bar);
         const int r = *(volatile int *)&gs.claim2;
@@ -223,7 +236,7 @@ __device__ void work_task(const PersistCtx &pc, bool own, int t, const PersistJo
     if (leader) {
         atomicExch(&pc.slot_task[slot], -1);
         __threadfence();
-        if (!wait_until_zero(&tk.helpers, PERSIST_SPIN_LIMIT)) atomicExch(&pc.q->error, DIL_ETIMEOUT);
+        if (!wait_until_zero(&tk.helpers, pc.spin_limit)) wait_failed(pc, tk);
         // no accepting repetition: the cap was reached, or the host canceled the launch
         gs.claim2 = (atomicOr(&tk.best_r, 0) != INT_MAX) ? 0 : ld_l2(&pc.q->cancel) ? 2 : 1;
     }
@@ -247,14 +260,16 @@ __device__ void work_task(const PersistCtx &pc, bool own, int t, const PersistJo
 template <int P, int ONLY>
 __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQueue *q, PersistTask *tasks,
                                                          int *slot_task, int32_t *scratch, int slot_polys,
-                                                         int max_iter_override, int chunk, int spec) {
+                                                         int max_iter_override, int chunk, int spec,
+                                                         int spin_limit) {
     extern __shared__ __align__(16) uint8_t smem[];
     const CtaView v = cta_setup<P>(smem);
     GroupSmem &gs = *v.gs;
     WarpSmem &ws = *v.ws;
     const int g = v.g, bar = v.bar, lane = v.lane;
     const bool leader = g == 0 && lane == 0;
-    PersistCtx pc{q, tasks, slot_task, scratch, slot_polys, (int)gridDim.x * v.groups, max_iter_override, spec};
+    PersistCtx pc{q, tasks, slot_task, scratch, slot_polys, (int)gridDim.x * v.groups, max_iter_override, spec,
+                  spin_limit};
     const int slot = blockIdx.x * v.groups + v.group;
     int32_t *mine = scratch + (size_t)slot * slot_polys * N;
     // One scheduling loop: fresh tasks from the queue (owned; after a host
@@ -364,6 +379,22 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
     }
 }
 
+// Runs after the persistent grid: every task whose bounded wait ran out ends
+// with status DIL_ETIMEOUT, 0 repetitions and a zeroed signature (nothing of
+// the launch writes to it any more).  One thread per task.
+__global__ void k_persist_finalize(PersistJobs J, const PersistTask *tasks) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < J.total; t += gridDim.x * blockDim.x) {
+        if (!tasks[t].fail) continue;
+        int local;
+        const PersistJob &jb = job_of(J, t, local);
+        const int sigb = jb.level == 2 ? Lv<2>::SIG : jb.level == 3 ? Lv<3>::SIG : Lv<5>::SIG;
+        uint8_t *sig = jb.sig + (size_t)local * sigb;
+        for (int b = 0; b < sigb; ++b) sig[b] = 0;
+        if (jb.status) jb.status[local] = DIL_ETIMEOUT;
+        if (jb.iters) jb.iters[local] = 0;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 namespace {
 
@@ -378,7 +409,8 @@ int slot_polys_for(const PersistJobs &J) {
     return m + PERSIST_META_POLYS;
 }
 
-using PersistKernel = void (*)(PersistJobs, PersistQueue *, PersistTask *, int *, int32_t *, int, int, int, int);
+using PersistKernel = void (*)(PersistJobs, PersistQueue *, PersistTask *, int *, int32_t *, int, int, int, int,
+                               int);
 
 // The kernel for a launch: one-warp groups whose jobs share one level get
 // that level's kernel, everything else the all-level one.
@@ -445,7 +477,7 @@ size_t persist_workspace_bytes(const PersistJobs &J, const PersistTuning &t, int
 }
 
 cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTuning &t, int max_iter_override,
-                                int device, cudaStream_t s) {
+                                int spin_limit, int device, cudaStream_t s) {
     if (J.total <= 0) return cudaSuccess;
     Layout L;
     cudaError_t e = layout_of(J, t, device, L);
@@ -455,6 +487,8 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(base + L.slots, 0xFF, (size_t)L.nslots * sizeof(int), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(base + L.tasks, 0, (size_t)J.total * sizeof(PersistTask), s);   // clears every fail flag
+    if (e != cudaSuccess) return e;
     auto *q = reinterpret_cast<PersistQueue *>(base + L.q);
     auto *tasks = reinterpret_cast<PersistTask *>(base + L.tasks);
     auto *slot_task = reinterpret_cast<int *>(base + L.slots);
@@ -462,8 +496,13 @@ cudaError_t launch_sign_persist(const PersistJobs &J, void *ws, const PersistTun
     const size_t smem = cta_bytes(t.warps, t.p);
     const int chunk = t.chunk > 0 ? t.chunk : 1;
     const PersistKernel kern = kernel_for(J, t.p);
+    const int limit = (spin_limit > 0 && spin_limit < PERSIST_SPIN_LIMIT) ? spin_limit : PERSIST_SPIN_LIMIT;
     kern<<<L.grid, t.warps * 32, smem, s>>>(J, q, tasks, slot_task, scratch, L.slot_polys, max_iter_override, chunk,
-                                            t.spec);
+                                            t.spec, limit);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int fin_blocks = (J.total + 255) / 256 < 4 * L.grid ? (J.total + 255) / 256 : 4 * L.grid;
+    k_persist_finalize<<<fin_blocks, 256, 0, s>>>(J, tasks);
     return cudaGetLastError();
 }
 

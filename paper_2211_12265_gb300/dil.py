@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
                 "dil_test_keccak_rate": [P, I, P],
                 "dil_test_sign_split": [P, I, S, P, P, P, P, P, P, P, P],
                 "dil_test_bounded_wait": [P, I, I, P],
+                "dil_test_set_spin_limit": [P, I],
                 "dil_sign_persistent": [P, I, P, P],
                 "dil_set_persistent_tuning": [P, I, I, I, I, I],
                 "dil_persistent_status": [P, P],
@@ -304,6 +305,11 @@ def dil_test_bounded_wait(ctx, flag_value: int, limit: int) -> int:
     r = ctypes.c_int()
     _check(load().dil_test_bounded_wait(ctx, flag_value, limit, ctypes.byref(r)), "dil_test_bounded_wait")
     return r.value
+
+
+def dil_test_set_spin_limit(ctx, limit: int) -> None:
+    """Polls per bounded device wait of later persistent launches (0 = default)."""
+    _check(load().dil_test_set_spin_limit(ctx, int(limit)), "dil_test_set_spin_limit")
 
 
 ISSUE_OPS = {"lop3": 0, "shf": 1, "imul": 2, "imul_hi": 3, "shfl": 4}

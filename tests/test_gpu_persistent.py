@@ -52,6 +52,43 @@ def _persistent(torch, ctx, jobs, reps=1):
     return [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy()) for o in outs]
 
 
+@pytest.mark.parametrize("tuning", [(8, 1, 0, 1, 8), (8, 2, 0, 1, 4)])
+def test_timed_out_waits_leave_defined_task_outputs(torch_cuda, tuning):
+    """A test-only limit of one poll per bounded wait makes the real waits
+    (the commit lock, an owner waiting for its helpers) run out under ordinary
+    contention.  The launch then reports DIL_ETIMEOUT; every task a wait ran
+    out on ends with status DIL_ETIMEOUT, 0 repetitions and a zeroed
+    signature; every other task equals the plain form byte for byte; and the
+    next launch on the same context, back at the default limit, is normal.
+    The waits only return early: nothing here can hang the GPU."""
+    from paper_2211_12265_gb300 import dil
+    j = _job_inputs(torch_cuda, 2, 12000, 35)        # about 2.5 waves: early tasks have no helpers
+    ref_sig, ref_st, ref_it = _plain(torch_cuda, j)
+    assert (ref_st == 0).all()
+    with dil.Context(0) as ctx:
+        dil.dil_set_persistent_tuning(ctx.handle, *tuning)
+        dil.dil_test_set_spin_limit(ctx.handle, 1)
+        sig = torch_cuda.full((j["n"], dil.SIZES[2][2]), 0x5A, dtype=torch_cuda.uint8, device="cuda")
+        st = torch_cuda.full((j["n"],), 9, dtype=torch_cuda.int32, device="cuda")
+        it = torch_cuda.full((j["n"],), 77, dtype=torch_cuda.int32, device="cuda")
+        desc = [dil.sign_job(2, j["n"], j["sk"], j["msg"], j["off"], sig, st, it)]
+        dil.dil_sign_persistent(ctx.handle, desc)
+        launch_status = dil.dil_persistent_status(ctx.handle)
+        sig_n, st_n, it_n = sig.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy()
+        timed = st_n == dil.ETIMEOUT
+        assert set(np.unique(st_n).tolist()) <= {dil.OK, dil.ETIMEOUT}
+        assert launch_status == (dil.ETIMEOUT if timed.any() else dil.OK)
+        assert timed.any(), "no wait ran out: the test did not reach the timeout path"
+        assert (sig_n[timed] == 0).all() and (it_n[timed] == 0).all()
+        done = ~timed
+        assert done.sum() > j["n"] // 4
+        assert np.array_equal(sig_n[done], ref_sig[done]) and np.array_equal(it_n[done], ref_it[done])
+        dil.dil_test_set_spin_limit(ctx.handle, 0)
+        (got,) = _persistent(torch_cuda, ctx, [j])
+    for a, b in zip(got, (ref_sig, ref_st, ref_it)):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("tuning", [(8, 2, 0, 1, 4), (4, 1, 0, 1, 0), (4, 1, 0, 3, 2), (8, 4, 2, 2, 8),
                                     (2, 2, 1, 1, 1), (8, 1, 0, 1, 8), (1, 1, 0, 1, 16)])
 def test_single_job_matches_plain(torch_cuda, tuning):
