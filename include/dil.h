@@ -107,13 +107,19 @@ int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8
  * afford cudaMalloc/cudaFree (both may synchronise the device), or code that
  * must not fail with out-of-memory mid-request.  Same arguments and results as
  * dil_sign without a context; runs on the current device with the default
- * repetition cap.  Scratch is a 64 MiB array inside the library's device image
- * (held by every GPU that loads the library until exit), so n may not exceed
+ * repetition cap and a fixed launch shape (4 warps per CTA, one warp per
+ * task).  Scratch is a 64 MiB array inside the library's device image (held
+ * by every GPU that loads the library until exit), so n may not exceed
  * 1110 / 789 / 532 tasks for levels 2 / 3 / 5: larger n returns DIL_EINVAL.
- * The first call on a device looks up the array's address (cudaGetSymbolAddress)
- * and should come before any stream capture.  All calls share the array: calls
- * that overlap on the GPU race and must be serialised.  Nothing in it needs
- * clearing (each task's scratch is written before it is read). */
+ * Set-up: the first call on a device looks up the array's address
+ * (cudaGetSymbolAddress), loads the Sign kernels and runs each once on no
+ * tasks, then synchronises `stream`; dil_sign_noalloc(level, 0, NULL, NULL,
+ * NULL, NULL, NULL, stream) does only that.  Make that call before any stream
+ * capture and before the first request that must not allocate.  The address
+ * is cached per device: do not use this entry point on a device after
+ * cudaDeviceReset.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised.  Nothing in it needs clearing (each task's
+ * scratch is written before it is read). */
 int dil_sign_noalloc(int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
                      uint8_t *sig, int32_t *task_status, void *stream);
 

@@ -9,10 +9,19 @@
 // array of NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
 // until the process exits.
 //
-// Set-up: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress and caches it per device;
-// that first call should come before any stream capture.  Every later call
-// reuses the cached address and allocates nothing.
+// Set-up: the first call on a device (with that device current; a call with
+// n = 0 does only this) looks up the array's device address with
+// cudaGetSymbolAddress, caches it per device, loads the Sign kernels of the
+// three levels and runs each once on no tasks, so that their code and their
+// local-memory reservation are in place before the first real request.  That
+// first call synchronises its stream and should come before any stream
+// capture.  Every later call reuses the cached address and allocates nothing.
+// The cache is per device ordinal: after cudaDeviceReset the array may move,
+// so this entry point must not be used on a device that was reset.
+//
+// Launch shape: 4 warps per CTA, one warp per task (every level), whatever
+// the context tuning says; the autotuned plain Sign shapes also use one warp
+// per task and lie within about 1% of it.
 //
 // The array is shared by every call and keeps the previous call's contents.
 // The Sign kernel writes every scratch word of a task before it reads it, so
@@ -32,11 +41,14 @@ constexpr int MAX_DEVICES = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
+constexpr int NOALLOC_WARPS = 4;   // warps per CTA; one warp per task
+
 std::mutex g_setup_mu;
 void *g_scratch_addr[MAX_DEVICES] = {};
 
-// Device address of g_noalloc_scratch on the current device (set-up on first use).
-int scratch_address(void **out) {
+// Device address of g_noalloc_scratch on the current device; the first use on
+// a device also warms the three Sign kernels on stream s.
+int scratch_address(void **out, cudaStream_t s) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
@@ -46,6 +58,9 @@ int scratch_address(void **out) {
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        for (int level : {2, 3, 5})
+            if (e == cudaSuccess) e = dil::warm_sign(level, NOALLOC_WARPS, 1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return DIL_ECUDA;
@@ -61,17 +76,17 @@ int scratch_address(void **out) {
 extern "C" int dil_sign_noalloc(int level, size_t n, const uint8_t *sk, const uint8_t *msg,
                                 const uint64_t *msg_off, uint8_t *sig, int32_t *task_status, void *stream) {
     if (level != 2 && level != 3 && level != 5) return DIL_EINVAL;
-    if (n == 0) return DIL_OK;
-    if (!sk || !msg_off || !sig) return DIL_EINVAL;
     const size_t per_task = dil::scratch_polys(dil::OP_SIGN, level) * 256 * sizeof(int32_t);
     if (n > NOALLOC_SCRATCH_BYTES / per_task) return DIL_EINVAL;   // beyond the static scratch
     void *scratch = nullptr;
-    int rc = scratch_address(&scratch);
-    if (rc != DIL_OK) return rc;
+    int rc = scratch_address(&scratch, (cudaStream_t)stream);   // set-up on a device's first call
+    if (rc != DIL_OK || n == 0) return rc;
+    if (!sk || !msg_off || !sig) return DIL_EINVAL;
     const int l = level == 2 ? 4 : level == 3 ? 5 : 7;
     const int max_iter = (65536 - l) / l + 1;   // cap implied by the 16-bit nonce
     cudaError_t e = dil::launch_sign(level, (int)n, sk, msg, msg_off, sig, task_status, nullptr,
-                                     static_cast<int32_t *>(scratch), max_iter, 4, 1, (cudaStream_t)stream);
+                                     static_cast<int32_t *>(scratch), max_iter, NOALLOC_WARPS, 1,
+                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return DIL_ECUDA;
     return DIL_OK;
 }

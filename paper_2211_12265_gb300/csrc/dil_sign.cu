@@ -52,4 +52,25 @@ cudaError_t launch_sign(int level, int n, const uint8_t *sk, const uint8_t *msg,
     DIL_DISPATCH(k_sign, sk, msg, off, sig, status, iters, scratch, max_iter)
 }
 
+namespace {
+template <class Kern>
+cudaError_t warm(Kern kern, int warps, int p, cudaStream_t s) {
+    const size_t smem = cta_bytes(warps, p);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // n = 0: every group returns before it touches a pointer
+    kern<<<1, warps * 32, smem, s>>>(0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t warm_sign(int level, int warps, int p, cudaStream_t s) {
+    switch (level * 10 + p) {
+        case 21: return warm(k_sign<2, 1>, warps, p, s);
+        case 31: return warm(k_sign<3, 1>, warps, p, s);
+        case 51: return warm(k_sign<5, 1>, warps, p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace dil
