@@ -180,27 +180,57 @@ __device__ __forceinline__ void absorb_smem(uint32_t &lo, uint32_t &hi, const ui
     keccak_f(lo, hi);
 }
 
-// Absorbs the concatenation A || B where A (lenA bytes) is in shared memory and
-// B (lenB bytes, any alignment) is in global memory; pads and permutes.  B is
-// read with coherent loads: it may have been written earlier by the same warp.
+// Aligned 8-byte word of global memory, loaded through L2: coherent with
+// stores and copies made while the kernel runs (a serving kernel reuses its
+// request buffers), unlike the L1 and read-only paths.
+__device__ __forceinline__ uint64_t ld_word_cg(const uint8_t *p) {
+    return __ldcg(reinterpret_cast<const unsigned long long *>(p));
+}
+
+// Absorbs the concatenation A || B where A (lenA bytes, a multiple of 8) is in
+// 8-byte-aligned shared memory and B (lenB bytes, any alignment) is in global
+// memory; pads and permutes.  B is read in aligned 8-byte words through L2,
+// one per lane and block (the section 3.3 wide, aligned input loads): lane i
+// takes word i of the block and its neighbour's by a shuffle and realigns
+// the pair with a funnel shift; the next block's words are loaded before the
+// current block is permuted.  An aligned word that holds a byte of B lies in
+// the same page as that byte, so no load can fault; bytes outside B are
+// masked off.
 __device__ __forceinline__ void absorb_concat(uint32_t &lo, uint32_t &hi, const uint8_t *A, int lenA,
                                               const uint8_t *B, size_t lenB, int rate, int lane) {
     const int words = rate / 8;
     const size_t total = (size_t)lenA + lenB;
+    const int shift = 8 * (int)((uintptr_t)B & 7);             // bit offset of B in its aligned word
+    const uint8_t *base = B - (shift >> 3);
+    // aligned words holding bytes of B (none when B is empty: B may point past its buffer)
+    const long long nwords = lenB ? (long long)((lenB + (shift >> 3) + 7) >> 3) : 0;
+    // lane k's aligned word of B for a block starting at concatenation byte
+    // `off`: index (off - lenA) / 8 + k; words outside B read as 0
+    auto word_at = [&](size_t off) -> uint64_t {
+        const long long j = ((long long)off - lenA) / 8 + lane;
+        return (j >= 0 && j < nwords) ? ld_word_cg(base + 8 * j) : 0ull;
+    };
     size_t off = 0;
+    uint64_t cur = word_at(0);
     for (;;) {
-        size_t rem = total - off;
-        bool last = rem < (size_t)rate;
+        const size_t rem = total - off;
+        const bool last = rem < (size_t)rate;
+        const uint64_t nxt = __shfl_down_sync(FULL, cur, 1);
+        const uint64_t ahead = last ? 0ull : word_at(off + rate);   // in flight during the permutation
         if (lane < words) {
-            uint64_t w = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                size_t p = off + 8 * lane + b;
-                if (p < total) {
-                    uint32_t v = (p < (size_t)lenA) ? A[p] : B[p - lenA];
-                    w |= (uint64_t)v << (8 * b);
-                }
+            const size_t p = off + 8 * lane;
+            uint64_t w;
+            if (p < (size_t)lenA) {
+                const uint2 v = *reinterpret_cast<const uint2 *>(A + p);
+                w = ((uint64_t)v.y << 32) | v.x;
+            } else {
+                w = shift ? (cur >> shift) | (nxt << (64 - shift)) : cur;
             }
+            const long long have = (long long)total - (long long)p;   // bytes of the word inside A || B
+            if (have <= 0)
+                w = 0;
+            else if (have < 8)
+                w &= (1ull << (8 * have)) - 1;
             if (last) pad_word(w, (int)rem, rate, lane);
             lo ^= (uint32_t)w;
             hi ^= (uint32_t)(w >> 32);
@@ -208,6 +238,7 @@ __device__ __forceinline__ void absorb_concat(uint32_t &lo, uint32_t &hi, const 
         keccak_f(lo, hi);
         if (last) break;
         off += rate;
+        cur = ahead;
     }
 }
 

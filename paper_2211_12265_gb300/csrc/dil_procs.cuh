@@ -811,7 +811,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     volatile int *vflag = &gs.flag;
     int32_t r[8], acc[8], ch[8];
     if (g == 0) {
-        gs.ctilde[lane] = __ldg(sig + lane);
+        gs.ctilde[lane] = __ldcg(sig + lane);
         gs.rho[lane] = __ldg(pk + lane);
         // strict hint decoding into bit masks
         stage_bytes(ws.sq, sig + V::SIG_H, V::OMEGA + V::K, lane);

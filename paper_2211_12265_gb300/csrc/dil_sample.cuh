@@ -572,9 +572,10 @@ __device__ __forceinline__ void pack8(uint8_t *out, const uint32_t v[8]) {
     }
 }
 
-// Copies nbytes from global to shared memory, one byte per lane per step.
+// Copies nbytes from global to shared memory, one byte per lane per step,
+// through L2 (coherent with copies into the source made while the kernel runs).
 __device__ __forceinline__ void stage_bytes(uint8_t *dst, const uint8_t *__restrict__ src, int nbytes, int lane) {
-    for (int i = lane; i < nbytes; i += 32) dst[i] = __ldg(src + i);
+    for (int i = lane; i < nbytes; i += 32) dst[i] = __ldcg(src + i);
 }
 
 }  // namespace dil
