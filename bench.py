@@ -9,16 +9,24 @@ L2 is flushed (512 MiB write) before every step.  ``value`` is
 (signs + verifies) per second over all ranks; ``e2e`` is the same through the
 host-buffer C entry points with the copies inside the timed region.
 
-The same line carries the persistent form of Sign on the same batch (device
-work queue, speculative nonces, CUDA graph) and a served measurement (the
-continuous-batching server over 4096 resident keys per level, mixed 60%
-verify / 40% sign requests of all levels, messages 32 B..16 KB): saturated
-ops/s and p50/p99 latency at half and 90% of saturation.
+The same line carries every other benchmark configuration, each measured
+in the same run:
+  * ``forms``: the persistent form of Sign on the same batch (device work
+    queue, speculative nonces, CUDA graph), the split-kernel ablation, and
+    ``level3`` / ``level5``: Dilithium3 and Dilithium5, 10,000 tasks each with
+    messages of 32..4096 bytes, plain and persistent Sign, Verify, KeyGen;
+    ``mixed_200k``: persistent Sign of 100,000 Dilithium2 + 100,000
+    Dilithium5 tasks in one launch against the plain one-launch-per-level
+    form;
+  * ``served``: the continuous-batching server over 4096 resident keys per
+    level (mixed 60% verify / 40% sign requests of all levels, messages
+    32 B..16 KB, Poisson arrivals): saturated ops/s, an arrival-rate sweep
+    with p50/p99 latency, at each rate the best p99 of the static-batching
+    service over a grid of (min_batch, max_wait), and the plain kernels'
+    rate on the same requests (one launch per operation and level).
 
-Other workloads: ``--workload level3|level5`` (10,000 tasks, messages of
-32..4096 bytes), ``--workload mixed`` (persistent Sign of 100,000 Dilithium2 +
-100,000 Dilithium5 tasks in one launch against the plain form) and
-``--workload serving`` (arrival-rate sweep of the served mix to saturation).
+``--workload level3|level5|mixed|serving`` runs one of those alone with its
+own JSON line.
 
 ``--impl reference`` times the CPU oracle (test infrastructure) on a bounded
 sample of the same workload on the host cores.
@@ -52,9 +60,16 @@ PAPER_A100 = {2: {"sign_ops_s": 574953, "verify_ops_s": 1408703},
               5: {"sign_ops_s": 315900, "verify_ops_s": 637299}}
 SMS = 152
 SM_MAX_MHZ = 2070.0
+# Integer-issue ceiling of one SM: 4 SM sub-partitions, each issuing at most one
+# warp instruction (32 thread-operations) per clock.  The ALU pipe alone (LOP3,
+# shifts) takes 2 warp instructions per SM clock (64 thread-ops), as ncu's
+# sm__inst_executed_pipe_alu.avg.peak_sustained reads on GB300.
+ISSUE_THREAD_OPS_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 512 << 20
 
-STATIC_BATCH, STATIC_WAIT_S = 4096, 0.05   # static batching of the served comparison
+# static batching (the plain one-launch-per-batch service): grid searched per arrival rate
+STATIC_GRID = [(mb, w) for mb in (128, 512, 2048) for w in (0.0005, 0.002, 0.008)]
+SERVED_FRACTIONS = (0.25, 0.5, 0.75, 0.9)
 
 WORKLOADS = {
     "level2": dict(level=2, n=10000, config=2),
@@ -179,7 +194,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle
-def cpu_baseline(level: int, wl: dict, budget_s: float = 15.0) -> dict:
+def cpu_baseline(level: int, wl: dict, budget_s: float = 10.0) -> dict:
     """Times the CPU oracle (as it stands) on a bounded sample of the workload:
     Sign then Verify of `sample` tasks on all host cores."""
     from oracle import oracle
@@ -322,7 +337,14 @@ def run_ours(args, ranks: Ranks) -> dict | None:
         if i >= 2:
             kg_ms.append(ev[0].elapsed_time(ev[1]))
     k_gen_ms = ranks.max(float(np.mean(kg_ms)))
-    served = served_summary(dev) if ranks.world == 1 else None
+
+    # the other configurations, each in its own launch configuration
+    timed = _timer(torch, flush, stream, ranks)
+    extra = max(1, min(args.steps, 10))
+    other_levels = {f"level{lv}": level_forms(ctx, lv, timed, stream, ranks, extra) for lv in (3, 5) if lv != level}
+    mixed = mixed_forms(ctx, timed, stream, ranks, max(1, min(args.steps, 5)))
+    ctx.apply_tuning()
+    served = served_measure(dev) if ranks.world == 1 else None
 
     # e2e: host buffers through the host-form C entry points
     h_sk = torch.empty_like(sk, device="cpu").pin_memory()
@@ -359,7 +381,13 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     achieved = ops / (sign_mean_ms * 1e-3) / 1e12
     lop3_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["lop3"])   # thread-ops / SM / clk
     shfl_rate = dil.dil_test_issue_rate(ctx.handle, dil.ISSUE_OPS["shfl"])
-    peak = SMS * lop3_rate * SM_MAX_MHZ * 1e6 / 1e12
+    keccak_forms = {name: dil.dil_test_keccak_rate(ctx.handle, form)
+                    for name, form in (("one_state_25_lanes", 1), ("two_states_interleaved", 2),
+                                       ("six_states_row_layout", 6), ("sixteen_states_two_threads", 16))}
+    peak = SMS * ISSUE_THREAD_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    alu_peak = SMS * lop3_rate * SM_MAX_MHZ * 1e6 / 1e12
+    for r in other_levels.values():
+        r["roofline_frac"] = r["sign_int_ops"] / (r["sign_ms"] * 1e-3) / 1e12 / peak
     traffic = load_traffic(level, n)
     hbm = measured_hbm_gbs()
     table = autotune.load() or {}
@@ -388,7 +416,8 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                                                                   * 1e-3),
                   "persistent_sign_ms": p_sign_ms,
                   "split_sign_ops_s": ranks.world * n / (s_sign_ms * 1e-3), "split_sign_rounds": rounds,
-                  "split_note": "fusion ablation: precompute kernel + two kernels per repetition round"},
+                  "split_note": "fusion ablation: precompute kernel + two kernels per repetition round",
+                  **other_levels, "mixed_200k": mixed},
         "served": served,
         "breakdown": {"sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
                       "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),
@@ -408,9 +437,13 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                      "dram_gbs": traffic / (sign_mean_ms * 1e-3) / 1e9 if traffic else None,
                      "dram_frac_of_measured_hbm": (traffic / (sign_mean_ms * 1e-3) / 1e9 / hbm
                                                    if traffic and hbm else None),
-                     "peak_basis": f"{SMS} SMs x {lop3_rate:.1f} LOP3 thread-ops/SM/clk (measured live) x "
-                                   f"{SM_MAX_MHZ:.0f} MHz max SM clock",
-                     "shfl_thread_ops_per_sm_clk": shfl_rate},
+                     "peak_basis": f"{SMS} SMs x 4 sub-partitions x one 32-thread warp instruction per clock "
+                                   f"({ISSUE_THREAD_OPS_PER_SM_CLK} thread-ops/SM/clk) x {SM_MAX_MHZ:.0f} MHz max SM clock",
+                     "alu_pipe": {"lop3_thread_ops_per_sm_clk": lop3_rate, "peak": alu_peak,
+                                  "frac": achieved / alu_peak,
+                                  "basis": "LOP3 rate measured live (per-SM clock64 spans) x SMs x max SM clock"},
+                     "shfl_thread_ops_per_sm_clk": shfl_rate,
+                     "keccak_sm_clk_per_state_round": keccak_forms},
         "clocks": clocks,
         "tuning": {"plain": table.get("plain", {}).get(str(level)),
                    "persistent": table.get("persistent", {}).get(str(level)),
@@ -423,59 +456,11 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     return res
 
 
-def served_summary(dev: int, n: int = 60000) -> dict:
-    """Saturated throughput and p50/p99 latency of the served mix (config 5)."""
-    from paper_2211_12265_gb300 import serving
-    keys = serving.make_keys((2, 3, 5), n_keys=4096, device=dev)
-    with serving.Server(dev, memory_budget=8 << 30, streams=4, max_batch=4096) as srv:
-        for lv in keys:
-            srv.add_keys(lv, *keys[lv])
-        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=100))      # warm-up
-        sat = serving.summarize(req := serving.serving_workload(keys, n, rate=1e9, seed=101), srv.replay(req))
-        rows = []
-        for i, f in enumerate((0.5, 0.9)):
-            rq = serving.serving_workload(keys, n, rate=f * sat["ops_s"], seed=102 + i)
-            r = serving.summarize(rq, srv.replay(rq))
-            r["offered_fraction"] = f
-            rows.append(r)
-        # the same arrivals served by static batches (the plain one-launch-per-batch service)
-        srv.set_batching(STATIC_BATCH, STATIC_WAIT_S)
-        rq = serving.serving_workload(keys, n, rate=0.5 * sat["ops_s"], seed=102)
-        static = serving.summarize(rq, srv.replay(rq))
-        static["offered_fraction"] = 0.5
-    return {"saturated_ops_s": sat["ops_s"], "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB log-uniform, "
-                                                     "4096 resident keys per level, Poisson arrivals",
-            "streams": 4, "at_load": rows,
-            "static_batching": {"min_batch": STATIC_BATCH, "max_wait_s": STATIC_WAIT_S, "at_load": [static]}}
-
-
-def run_mixed(args, ranks: Ranks) -> dict:
-    """Config 4: persistent Sign of 100,000 Dil2 + 100,000 Dil5 tasks (one
-    graph-captured launch) against the plain one-launch-per-level form."""
-    import torch
-
-    from paper_2211_12265_gb300 import dil
-    n = args.n or 100000
-    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
-    torch.cuda.set_device(dev)
-    ctx = dil.Context(dev)
-    ctx.apply_tuning()
-    data = {}
-    for level in (2, 5):
-        wl = W.workload(4, n)
-        seeds = torch.from_numpy(W.seeds(n, 4 + level, offset=ranks.rank * n)).cuda()
-        msg = torch.from_numpy(wl["msg"]).cuda()
-        off = torch.from_numpy(wl["msg_off"]).cuda()
-        pk, sk = ctx.keygen(level, seeds)
-        sig = torch.empty((n, dil.SIZES[level][2]), dtype=torch.uint8, device="cuda")
-        st = torch.empty(n, dtype=torch.int32, device="cuda")
-        data[level] = (sk, msg, off, sig, st)
-    jobs = [dil.sign_job(2, n, *data[2]), dil.sign_job(5, n, *data[5])]
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    def timed(fn, steps):
-        for _ in range(max(args.warmup, 3)):
+def _timer(torch, flush, stream, ranks):
+    """Mean CUDA-event time (ms) of fn over `steps` runs, L2 flushed before
+    each, after `warm` untimed runs; maximum over ranks."""
+    def timed(fn, steps, warm=3):
+        for _ in range(warm):
             fn()
         torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
@@ -487,59 +472,238 @@ def run_mixed(args, ranks: Ranks) -> dict:
             ev[1].record(stream)
         torch.cuda.synchronize()
         return ranks.max(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])))
-
-    steps = max(1, min(args.steps, 20))
-    t_p = timed(lambda: dil.dil_sign_persistent(ctx.handle, jobs, stream), steps)
-    assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK
-    t_plain = timed(lambda: (dil.dil_sign(ctx.handle, 2, n, *data[2], stream=stream),
-                             dil.dil_sign(ctx.handle, 5, n, *data[5], stream=stream)), steps)
-    ok = all(bool((data[lv][4] == 0).all()) for lv in (2, 5))
-    ctx.close()
-    return {"metric": METRIC, "value": ranks.world * 2 * n / (t_p * 1e-3), "unit": "ops/s", "n_gpus": ranks.world,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": t_p, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded PCG64 keys and messages)",
-            "config": {"workload": f"sign-{n}-dilithium2+{n}-dilithium5-persistent", "msg_bytes": 32,
-                       "form": "persistent, one graph-captured launch", "l2": "flushed before every step",
-                       "parallelism": f"replicas x{ranks.world}"},
-            "forms": {"persistent_ops_s": ranks.world * 2 * n / (t_p * 1e-3),
-                      "plain_ops_s": ranks.world * 2 * n / (t_plain * 1e-3), "persistent_ms": t_p,
-                      "plain_ms": t_plain, "all_signed": ok},
-            "gpu_launches": steps}
+    return timed
 
 
-def run_serving(args, ranks: Ranks) -> dict | None:
-    """Config 5: arrival-rate sweep of the served mix, 10% to 120% of saturation."""
+def level_forms(ctx, level: int, timed, stream, ranks, steps: int, n: int = 10000) -> dict:
+    """Config 3 at one level: 10,000 tasks with messages of 32..4096 bytes;
+    plain Sign, Verify and KeyGen (one launch each) and the persistent Sign."""
     import torch
 
+    from paper_2211_12265_gb300 import autotune, dil
+    wl = W.workload(3, n)
+    if ranks.rank:
+        wl["seeds"] = W.seeds(n, 3, offset=ranks.rank * n)
+    seeds = torch.from_numpy(wl["seeds"]).cuda()
+    msg = torch.from_numpy(wl["msg"]).cuda()
+    off = torch.from_numpy(wl["msg_off"]).cuda()
+    pk, sk = ctx.keygen(level, seeds)
+    sig, st, its = ctx.sign(level, sk, msg, off, iterations=True)
+    ok = ctx.verify(level, pk, msg, off, sig)
+    torch.cuda.synchronize()
+    assert bool((st == 0).all()) and bool(ok.all())
+    t_sign = timed(lambda: dil.dil_sign(ctx.handle, level, n, sk, msg, off, sig, st, stream), steps)
+    t_ver = timed(lambda: dil.dil_verify(ctx.handle, level, n, pk, msg, off, sig, ok, stream), steps)
+    t_kg = timed(lambda: dil.dil_keygen(ctx.handle, level, n, seeds, pk, sk, stream), steps)
+    autotune.apply(ctx, persistent_level=level)
+    job = [dil.sign_job(level, n, sk, msg, off, sig, st)]
+    t_p = timed(lambda: dil.dil_sign_persistent(ctx.handle, job, stream), steps)
+    assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK and bool((st == 0).all())
+    assert bool(ok.all())
+    iters = its.cpu().numpy()
+    w = ranks.world
+    return {"workload": f"dilithium{level}-{n}", "msg_bytes": f"{int(wl['lengths'].min())}-{int(wl['lengths'].max())}",
+            "plain_sign_ops_s": w * n / (t_sign * 1e-3), "persistent_sign_ops_s": w * n / (t_p * 1e-3),
+            "verify_ops_s": w * n / (t_ver * 1e-3), "keygen_ops_s": w * n / (t_kg * 1e-3),
+            "plain_step_ops_s": w * 2 * n / ((t_sign + t_ver) * 1e-3),
+            "persistent_step_ops_s": w * 2 * n / ((t_p + t_ver) * 1e-3),
+            "sign_ms": t_sign, "persistent_sign_ms": t_p, "verify_ms": t_ver, "keygen_ms": t_kg,
+            "mean_sign_repetitions": float(iters.mean()),
+            "sign_int_ops": WK.int_ops(WK.sign_work(level, iters, wl["lengths"])),
+            "paper_context_a100": PAPER_A100[level]}
+
+
+def mixed_forms(ctx, timed, stream, ranks, steps: int, n: int = 100000) -> dict:
+    """Config 4: persistent Sign of n Dilithium2 + n Dilithium5 tasks (one
+    graph-captured launch) against the plain form (one launch per level)."""
+    import torch
+
+    from paper_2211_12265_gb300 import autotune, dil
+    autotune.apply(ctx, persistent_level="mixed")
+    data = {}
+    for level in (2, 5):
+        wl = W.workload(4, n)
+        seeds = torch.from_numpy(W.seeds(n, 4 + level, offset=ranks.rank * n)).cuda()
+        msg = torch.from_numpy(wl["msg"]).cuda()
+        off = torch.from_numpy(wl["msg_off"]).cuda()
+        pk, sk = ctx.keygen(level, seeds)
+        sig = torch.empty((n, dil.SIZES[level][2]), dtype=torch.uint8, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        data[level] = (sk, msg, off, sig, st)
+    jobs = [dil.sign_job(2, n, *data[2]), dil.sign_job(5, n, *data[5])]
+    t_p = timed(lambda: dil.dil_sign_persistent(ctx.handle, jobs, stream), steps)
+    assert dil.dil_persistent_status(ctx.handle, stream) == dil.OK
+    assert all(bool((data[lv][4] == 0).all()) for lv in (2, 5))
+    t_plain = timed(lambda: (dil.dil_sign(ctx.handle, 2, n, *data[2], stream=stream),
+                             dil.dil_sign(ctx.handle, 5, n, *data[5], stream=stream)), steps)
+    assert all(bool((data[lv][4] == 0).all()) for lv in (2, 5))
+    w = ranks.world
+    return {"workload": f"sign-{n}-dilithium2+{n}-dilithium5, 32 B messages",
+            "persistent_ops_s": w * 2 * n / (t_p * 1e-3), "plain_ops_s": w * 2 * n / (t_plain * 1e-3),
+            "persistent_ms": t_p, "plain_ms": t_plain, "steps": steps}
+
+
+def plain_replay(dev: int, keys: dict, req: dict, reps: int = 5) -> dict:
+    """The requests of a served trace run by the plain kernels, one launch per
+    (operation, level) with the whole trace resident on the device: the
+    plain one-launch-per-batch form at its largest batch."""
+    import torch
+
+    from paper_2211_12265_gb300 import dil
+    groups = []
+    with dil.Context(dev) as ctx:
+        ctx.apply_tuning()
+        for op in (0, 1):
+            for lv in sorted(keys):
+                idx = np.nonzero((req["op"] == op) & (req["level"] == lv))[0]
+                if idx.size == 0:
+                    continue
+                parts = [req["msg"][req["msg_off"][i]:req["msg_off"][i + 1]] for i in idx]
+                o = np.zeros(idx.size + 1, dtype=np.uint64)
+                o[1:] = np.cumsum([p.size for p in parts])
+                m = torch.from_numpy(np.concatenate(parts + [np.zeros(1, np.uint8)])).cuda()
+                o = torch.from_numpy(o).cuda()
+                kidx = req["key"][idx]
+                sigb = dil.SIZES[lv][2]
+                if op == 0:
+                    sk = torch.from_numpy(np.ascontiguousarray(keys[lv][1][kidx])).cuda()
+                    sig = torch.empty((idx.size, sigb), dtype=torch.uint8, device="cuda")
+                    st = torch.empty(idx.size, dtype=torch.int32, device="cuda")
+                    groups.append(("sign", lv, idx.size, lambda lv=lv, sk=sk, m=m, o=o, sig=sig, st=st, k=idx.size:
+                                   dil.dil_sign(ctx.handle, lv, k, sk, m, o, sig, st)))
+                else:
+                    pk = torch.from_numpy(np.ascontiguousarray(keys[lv][0][kidx])).cuda()
+                    sg = torch.from_numpy(np.ascontiguousarray(req["sig_in"][idx, :sigb])).cuda()
+                    ok = torch.empty(idx.size, dtype=torch.uint8, device="cuda")
+                    groups.append(("verify", lv, idx.size, lambda lv=lv, pk=pk, m=m, o=o, sg=sg, ok=ok, k=idx.size:
+                                   dil.dil_verify(ctx.handle, lv, k, pk, m, o, sg, ok)))
+
+        def run():
+            for g in groups:
+                g[3]()
+        run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    t = float(np.median(ts))
+    n = int(req["op"].size)
+    return {"ops_s": n / (t * 1e-3), "ms": t, "requests": n, "launches": len(groups),
+            "form": "plain kernels, one launch per (operation, level), inputs resident on the device"}
+
+
+def served_measure(dev: int, n: int = 40000, fractions=SERVED_FRACTIONS) -> dict:
+    """Config 5: the served mix on the continuous-batching server: saturated
+    ops/s, an arrival-rate sweep with p50/p99, and at each rate the best p99
+    of static batching over STATIC_GRID; beside it the plain kernels' rate on
+    the saturated trace's requests."""
     from paper_2211_12265_gb300 import serving
-    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
-    torch.cuda.set_device(dev)
     keys = serving.make_keys((2, 3, 5), n_keys=4096, device=dev)
-    n = args.n or 60000
     with serving.Server(dev, memory_budget=8 << 30, streams=4, max_batch=4096) as srv:
         for lv in keys:
             srv.add_keys(lv, *keys[lv])
-        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=200))
-        req = serving.serving_workload(keys, n, rate=1e9, seed=201)
-        sat = serving.summarize(req, srv.replay(req))
-        fracs = (0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.2)
-        rows = serving.sweep(srv, keys, [f * sat["ops_s"] for f in fracs], n_per_rate=n, seed=210)
+        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=100))      # warm-up
+        sat_req = serving.serving_workload(keys, n, rate=1e9, seed=101)
+        sat = serving.summarize(sat_req, srv.replay(sat_req))
+        rows, static_rows = [], []
+        for i, f in enumerate(fractions):
+            rq = serving.serving_workload(keys, n, rate=f * sat["ops_s"], seed=102 + i)
+            srv.set_batching(1, 0.0)
+            r = serving.summarize(rq, srv.replay(rq))
+            r["offered_fraction"] = f
+            rows.append(r)
+            best = None
+            for mb, wait in STATIC_GRID:
+                srv.set_batching(mb, wait)
+                sr = serving.summarize(rq, srv.replay(rq))
+                sr.update({"min_batch": mb, "max_wait_s": wait})
+                if best is None or sr["p99_ms"] < best["p99_ms"]:
+                    best = sr
+            best["offered_fraction"] = f
+            best["grid_points"] = len(STATIC_GRID)
+            static_rows.append(best)
+        srv.set_batching(1, 0.0)
         batches, carried, launches = srv.stats()
-        # the same arrival traces served by static batches (the plain one-launch-per-batch service)
-        srv.set_batching(STATIC_BATCH, STATIC_WAIT_S)
-        static = serving.sweep(srv, keys, [f * sat["ops_s"] for f in (0.1, 0.5, 0.9)], n_per_rate=n, seed=210)
-    best = max(rows + [sat], key=lambda r: r["ops_s"])
+    plain = plain_replay(dev, keys, sat_req)
+    return {"saturated_ops_s": sat["ops_s"], "saturated": sat,
+            "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB log-uniform, 4096 resident keys per level, "
+                   "Poisson arrivals", "streams": 4, "sweep": rows,
+            "static_batching_best_p99": static_rows,
+            "static_grid": {"min_batch": sorted({g[0] for g in STATIC_GRID}),
+                            "max_wait_s": sorted({g[1] for g in STATIC_GRID})},
+            "plain_kernels_same_requests": plain,
+            "served_over_plain": sat["ops_s"] / plain["ops_s"],
+            "server_batches": batches, "server_requests": carried, "server_launches": launches}
+
+
+def run_mixed(args, ranks: Ranks) -> dict:
+    """Config 4 alone (``--workload mixed``)."""
+    import torch
+
+    from paper_2211_12265_gb300 import dil
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    ctx = dil.Context(dev)
+    ctx.apply_tuning()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    steps = max(1, min(args.steps, 20))
+    r = mixed_forms(ctx, _timer(torch, flush, stream, ranks), stream, ranks, steps, n=args.n or 100000)
+    ctx.close()
+    return {"metric": METRIC, "value": r["persistent_ops_s"], "unit": "ops/s", "n_gpus": ranks.world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": r["persistent_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded PCG64 keys and messages)",
+            "config": {"workload": r["workload"], "form": "persistent, one graph-captured launch",
+                       "l2": "flushed before every step", "parallelism": f"replicas x{ranks.world}"},
+            "forms": {"mixed_200k": r}, "gpu_launches": steps}
+
+
+def run_level(args, ranks: Ranks) -> dict:
+    """Config 3 at one level alone (``--workload level3|level5``)."""
+    import torch
+
+    from paper_2211_12265_gb300 import dil
+    spec = WORKLOADS[args.workload]
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    ctx = dil.Context(dev)
+    ctx.apply_tuning()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    steps = max(1, min(args.steps, 50))
+    r = level_forms(ctx, spec["level"], _timer(torch, flush, stream, ranks), stream, ranks, steps,
+                    n=args.n or spec["n"])
+    ctx.close()
+    return {"metric": METRIC, "value": r["plain_step_ops_s"], "unit": "ops/s", "n_gpus": ranks.world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": r["sign_ms"] + r["verify_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded PCG64 keys and messages)",
+            "config": {"workload": r["workload"] + "-sign+verify", "msg_bytes": r["msg_bytes"],
+                       "form": "plain, one launch per phase", "l2": "flushed before every step",
+                       "parallelism": f"replicas x{ranks.world}"},
+            "forms": {f"level{spec['level']}": r}, "gpu_launches": 2 * steps}
+
+
+def run_serving(args, ranks: Ranks) -> dict | None:
+    """Config 5 alone (``--workload serving``): a finer sweep, 10% to 120%."""
+    import torch
+    dev = ranks.local if torch.cuda.device_count() > ranks.local else 0
+    torch.cuda.set_device(dev)
+    r = served_measure(dev, n=args.n or 60000, fractions=(0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.2))
+    best = max(r["sweep"] + [r["saturated"]], key=lambda x: x["ops_s"])
     return {"metric": METRIC, "value": ranks.world * best["ops_s"], "unit": "ops/s", "n_gpus": ranks.world,
-            "steps": len(rows) + 1, "warmup": 1, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Poisson arrivals)",
-            "config": {"workload": "served-mix", "mix": "60% verify / 40% sign, levels 2/3/5, msg 32 B-16 KB "
-                                                        "log-uniform, 4096 resident keys per level",
-                       "requests_per_point": n, "streams": 4, "parallelism": f"replicas x{ranks.world}"},
-            "served": {"saturated": sat, "sweep": rows, "batches": batches, "requests": carried,
-                       "static_batching": {"min_batch": STATIC_BATCH, "max_wait_s": STATIC_WAIT_S,
-                                           "sweep": static}},
-            "gpu_launches": launches,
-            "gpu_launches_note": "keyed kernel launches of the warm-up, the saturated point and the continuous sweep"}
+            "steps": len(r["sweep"]) + 1, "warmup": 1, "ms_per_step": 1e3 * r["saturated"]["wall_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded Poisson arrivals)",
+            "config": {"workload": "served-mix", "mix": r["mix"], "requests_per_point": args.n or 60000,
+                       "streams": 4, "parallelism": f"replicas x{ranks.world}"},
+            "served": r, "gpu_launches": r["server_launches"],
+            "gpu_launches_note": "keyed kernel launches of the server over the whole run"}
 
 
 def measured_hbm_gbs():
@@ -573,7 +737,7 @@ def run_reference(args, ranks: Ranks) -> dict | None:
     spec = WORKLOADS[args.workload]
     level = spec["level"]
     cores = os.cpu_count() or 1
-    sample = max(cores * 2, 32)
+    sample = 64 * cores            # 64 tasks per host thread: the repetition counts average out per thread
     wl = W.workload(spec["config"], sample)
     pk, sk = oracle.keygen_batch(level, wl["seeds"], nthreads=cores)
     off, msg = wl["msg_off"], wl["msg"]
@@ -611,6 +775,8 @@ def main():
             res = run_reference(args, ranks)
         elif args.workload == "mixed":
             res = run_mixed(args, ranks)
+        elif args.workload in ("level3", "level5"):
+            res = run_level(args, ranks)
         elif args.workload == "serving":
             res = run_serving(args, ranks)
         else:

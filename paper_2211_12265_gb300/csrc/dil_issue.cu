@@ -1,11 +1,18 @@
-// Test-only probes.  dil_test_issue_rate: sustained issue rate of one
-// integer instruction class, in thread-operations per SM clock, measured with
-// clock64() over independent dependency chains at full occupancy (the
-// denominator of the integer roofline the benchmark reports).
-// dil_test_keccak_rate: SM clocks per state per round of the three
-// Keccak-f[1600] forms the kernels use, 32 warps per SM.
+// Test-only probes.  dil_test_issue_rate: sustained rate of one integer
+// instruction class, in thread-operations per SM clock, over independent
+// dependency chains at full occupancy.  dil_test_keccak_rate: SM clocks per
+// state per round of the four Keccak-f[1600] forms the kernels use, 32 warps
+// per SM.
+//
+// Timing: every block records its SM (%smid) and clock64() after a barrier
+// at its start and end; an SM's time is the span from the first start to the
+// last end of the blocks it ran (clock64 counts that SM's clock), and its work
+// is the sum of theirs.  Blocks of one SM need not run at the same time, so a
+// block's own window is not the SM's time.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
 #include <vector>
 
 #include "dil_keccak16.cuh"
@@ -15,6 +22,42 @@
 namespace dil {
 
 constexpr int PROBE_ITERS = 4096;
+
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
+// rec: 3 entries per block (SM id, start clock, end clock)
+__device__ __forceinline__ void record(long long *rec, long long t0, long long t1) {
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = sm_id();
+        rec[3 * blockIdx.x + 1] = t0;
+        rec[3 * blockIdx.x + 2] = t1;
+    }
+}
+
+// Per-SM work / per-SM span (first start to last end), averaged over SMs;
+// work_per_block in the caller's unit.
+double per_sm_rate(const std::vector<long long> &rec, int blocks, double work_per_block) {
+    std::map<long long, std::pair<long long, long long>> span;
+    std::map<long long, int> count;
+    for (int b = 0; b < blocks; ++b) {
+        const long long sm = rec[3 * b], t0 = rec[3 * b + 1], t1 = rec[3 * b + 2];
+        auto it = span.find(sm);
+        if (it == span.end()) {
+            span[sm] = {t0, t1};
+        } else {
+            it->second.first = std::min(it->second.first, t0);
+            it->second.second = std::max(it->second.second, t1);
+        }
+        ++count[sm];
+    }
+    double sum = 0;
+    for (auto &kv : span) sum += count[kv.first] * work_per_block / (double)(kv.second.second - kv.second.first);
+    return span.empty() ? 0.0 : sum / span.size();
+}
 
 template <int OP>
 __device__ __forceinline__ uint32_t probe_op(uint32_t a, uint32_t b, uint32_t c) {
@@ -42,7 +85,7 @@ __global__ void __launch_bounds__(1024) k_probe(uint32_t *out, long long *cyc) {
     }
     __syncthreads();
     long long t1 = clock64();
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    record(cyc, t0, t1);
     out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
 }
 
@@ -55,7 +98,7 @@ cudaError_t measure_issue_rate(int op, double *rate) {
     long long *cyc = nullptr;
     cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 4);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&cyc, (size_t)blocks * 8);
+    e = cudaMalloc(&cyc, (size_t)blocks * 3 * 8);
     if (e != cudaSuccess) {
         cudaFree(out);
         return e;
@@ -71,15 +114,12 @@ cudaError_t measure_issue_rate(int op, double *rate) {
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    std::vector<long long> h(blocks);
-    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost);
+    std::vector<long long> h(3 * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 3 * 8, cudaMemcpyDeviceToHost);
     cudaFree(out);
     cudaFree(cyc);
     if (e != cudaSuccess) return e;
-    double mean = 0;
-    for (long long v : h) mean += (double)v;
-    mean /= blocks;
-    *rate = 2.0 * threads * PROBE_ITERS * 8 / mean;
+    *rate = per_sm_rate(h, blocks, (double)threads * PROBE_ITERS * 8);
     return cudaSuccess;
 }
 
@@ -110,7 +150,7 @@ __global__ void __launch_bounds__(KPROBE_WARPS * 32, KPROBE_CTAS_PER_SM) k_kecca
     }
     __syncthreads();
     const long long t1 = clock64();
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    record(cyc, t0, t1);
     out[blockIdx.x * blockDim.x + threadIdx.x] = lo ^ hi ^ lo1 ^ hi1 ^ (FORM >= 6 ? kst[lane] : 0u);
 }
 
@@ -123,7 +163,7 @@ cudaError_t measure_keccak_rate(int form, double *clk_per_state_round) {
     long long *cyc = nullptr;
     cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 4);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&cyc, (size_t)blocks * 8);
+    e = cudaMalloc(&cyc, (size_t)blocks * 3 * 8);
     if (e != cudaSuccess) {
         cudaFree(out);
         return e;
@@ -136,16 +176,14 @@ cudaError_t measure_keccak_rate(int form, double *clk_per_state_round) {
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    std::vector<long long> h(blocks);
-    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost);
+    std::vector<long long> h(3 * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, (size_t)blocks * 3 * 8, cudaMemcpyDeviceToHost);
     cudaFree(out);
     cudaFree(cyc);
     if (e != cudaSuccess) return e;
-    double mean = 0;
-    for (long long v : h) mean += (double)v;
-    mean /= blocks;
-    // one SM runs KPROBE_CTAS_PER_SM CTAs at once; its clock covers all their state-rounds
-    *clk_per_state_round = mean / ((double)KPROBE_CTAS_PER_SM * KPROBE_WARPS * form * KPROBE_PERMS * 24);
+    // state-rounds per SM clock, inverted
+    const double rate = per_sm_rate(h, blocks, (double)KPROBE_WARPS * form * KPROBE_PERMS * 24);
+    *clk_per_state_round = rate > 0 ? 1.0 / rate : 0.0;
     return cudaSuccess;
 }
 
