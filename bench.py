@@ -607,7 +607,7 @@ def served_measure(dev: int, n: int = 40000, fractions=SERVED_FRACTIONS) -> dict
     with serving.Server(dev, memory_budget=8 << 30, streams=4, max_batch=4096) as srv:
         for lv in keys:
             srv.add_keys(lv, *keys[lv])
-        srv.replay(serving.serving_workload(keys, 8000, rate=1e9, seed=100))      # warm-up
+        srv.replay(serving.serving_workload(keys, n, rate=1e9, seed=100))         # warm-up (host buffers touched)
         sat_req = serving.serving_workload(keys, n, rate=1e9, seed=101)
         sat = serving.summarize(sat_req, srv.replay(sat_req))
         rows, static_rows = [], []

@@ -211,15 +211,22 @@ int dil_verify_keyed(dil_ctx *ctx, const dil_keystore *ks, size_t n, const int32
 
 /* ----------------------------------------------------------------------------
  * Serving loop (continuous batching).  A server owns resident key stores (one
- * per level), S CUDA streams ("slots") with device and pinned host buffers
- * sized from a memory budget, and a dispatcher thread.  Whenever a slot is
- * free and requests are pending, the dispatcher takes them in arrival order
- * (at most max_batch requests and the slot's message capacity), groups them
- * by operation and level, and runs the keyed kernels on that slot's stream,
- * so requests arriving while others run join the next free slot and batches
- * overlap on the device.  Results equal dil_sign / dil_verify's.  Latency is
- * measured from a request's arrival to the moment its result is visible to
- * the host.  All pointers of the server calls are HOST pointers.
+ * per level) and, from half of its memory budget each:
+ *   - a device request ring with a message arena, served by a resident
+ *     serving kernel (the default, continuous policy): a host thread copies
+ *     arriving requests into the ring and publishes them; the kernel's
+ *     one-warp workers take each request as soon as one is free (no batch
+ *     boundaries on the device), idle workers help unfinished Signs with
+ *     further nonces (the smallest accepting one is committed), and results
+ *     are written to mapped host memory and handed back as they complete.
+ *     The kernel exits after a few idle milliseconds and is relaunched when
+ *     requests arrive;
+ *   - S CUDA streams ("slots") with device and pinned host buffers for the
+ *     static policy (dil_server_set_batching), where a batch of requests runs
+ *     as keyed-kernel launches per operation and level.
+ * Results equal dil_sign / dil_verify's.  Latency is measured from a
+ * request's arrival to the moment its result is visible to the host.  All
+ * pointers of the server calls are HOST pointers.
  * ------------------------------------------------------------------------- */
 typedef struct dil_server dil_server;
 
@@ -235,26 +242,30 @@ typedef struct {
     double latency_s;    /* arrival to result visible on the host */
 } dil_result;
 
-/* Creates a server on `device` with `streams` slots (1..16).  The slots'
- * device buffers must fit memory_budget (0 = 4 GiB, key stores excluded):
- * max_batch is halved until they do (DIL_ENOMEM if even 1 does not fit). */
+/* Creates a server on `device` with `streams` slots (1..16).  memory_budget
+ * (0 = 4 GiB, key stores excluded) is split in two: the slots' device buffers
+ * must fit one half (max_batch is halved until they do; DIL_ENOMEM if even 1
+ * does not fit), the request ring, arena and serving workers are sized to the
+ * other (fewer workers when it is small). */
 int dil_server_create(int device, size_t memory_budget, int streams, int max_batch, dil_server **out);
 /* Stops the dispatcher after in-flight work, frees everything.  NULL accepted. */
 int dil_server_destroy(dil_server *srv);
 /* The admission limits chosen at creation. */
 int dil_server_limits(const dil_server *srv, int *max_batch, size_t *msg_capacity);
-/* Batching policy.  By default (max_wait_s = 0) a free slot takes whatever is
- * pending (continuous batching).  With max_wait_s > 0 a slot starts only when
- * at least min_batch requests are pending (capped by the admission limit) or
- * the oldest pending request has waited max_wait_s seconds: static batching,
- * the plain one-launch-per-batch service, kept for comparison.  DIL_EINVAL for
- * min_batch < 1 or a negative wait. */
+/* Batching policy.  By default (max_wait_s = 0) requests go to the device
+ * ring and the serving kernel (continuous batching).  With max_wait_s > 0 a
+ * slot starts only when at least min_batch requests are pending (capped by
+ * the admission limit) or the oldest pending request has waited max_wait_s
+ * seconds: static batching, the plain one-launch-per-batch service, kept for
+ * comparison (switching to it stops an idle serving kernel first).
+ * DIL_EINVAL for min_batch < 1 or a negative wait. */
 int dil_server_set_batching(dil_server *srv, int min_batch, double max_wait_s);
 
-/* Launch shape of the server's keyed kernels for one operation (0 = Sign,
- * 1 = Verify) and level: warps per CTA (1..8) and warps per task (1, 2, 4,
- * dividing the former).  Defaults: Sign 8 and 4, Verify 4 and 1.  Takes
- * effect for batches started afterwards.  DIL_EINVAL for other values. */
+/* Launch shape of the keyed kernels of static batches for one operation (0 =
+ * Sign, 1 = Verify) and level: warps per CTA (1..8) and warps per task (1, 2,
+ * 4, dividing the former).  Defaults: Sign 8 and 4, Verify 4 and 1.  Takes
+ * effect for batches started afterwards (the serving kernel always runs one
+ * warp per request).  DIL_EINVAL for other values. */
 int dil_server_set_tuning(dil_server *srv, int op, int level, int warps_per_cta, int warps_per_task);
 
 /* Installs n resident key pairs of one level (key ids 0..n-1), replacing the
@@ -280,9 +291,9 @@ int dil_server_poll(dil_server *srv, dil_result *out, size_t max_n, size_t *n_ou
 int dil_server_replay(dil_server *srv, size_t n, const double *arrival_s, const int32_t *op, const int32_t *level,
                       const int32_t *key, const uint8_t *msg, const uint64_t *msg_off, const uint8_t *sig_in,
                       uint8_t *sig_out, int32_t *status, uint8_t *ok, double *latency_s, double *wall_s);
-/* Batches dispatched, requests they carried and keyed-kernel launches (one
- * per (operation, level) group of a batch) since creation.  Any output
- * pointer may be NULL. */
+/* Batches dispatched (static batches and ring publications), requests they
+ * carried and kernel launches (keyed-kernel launches of static batches,
+ * serving-kernel launches) since creation.  Any output pointer may be NULL. */
 int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests, uint64_t *launches);
 
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;

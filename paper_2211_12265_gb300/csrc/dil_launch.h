@@ -132,6 +132,77 @@ cudaError_t persist_cancel(void *ws, cudaStream_t s);
 // Runs the scheduler's bounded wait on a flag holding flag_value (synchronous).
 cudaError_t test_bounded_wait(int flag_value, int limit, int *result_host);
 
+// ---------------------------------------------------------------- serving kernel
+// One request of the continuous-batching server, in the device request ring
+// (slot = ticket mod ring size), copied in by the host before it publishes
+// the ticket.
+struct __align__(16) ServeReq {
+    int32_t op;      // 0 = Sign, 1 = Verify
+    int32_t level;   // 2, 3 or 5
+    int32_t key;     // resident key index of that level
+    int32_t pad;
+    uint64_t msg;    // byte offset of the message in the arena
+    uint64_t mlen;
+    uint64_t sig;    // byte offset of the signature to verify in the arena
+    uint64_t pad2;   // 48 bytes: every slot 16-byte aligned
+};
+static_assert(sizeof(ServeReq) == 48, "ServeReq layout");
+// Control words of the serving kernel (device memory, one cache line each).
+struct ServeCtl {
+    int tail;          // tickets published by the host (written by its copies)
+    int pad0[31];
+    int head;          // next ticket to claim
+    int comp;          // completions issued (slots of the completion ring)
+    int error;         // DIL_ETIMEOUT when a bounded wait ran out
+    int pad1[29];
+    int stop;          // set by the host: workers exit once nothing is pending
+    int pad2[31];
+};
+// Per-request record of a Sign (ring slot): the scheduling state shared by
+// the owner and its helpers and the message's mu and rho'.  tref packs the
+// ticket (high 32 bits) with the number of workers holding the record (low
+// 32 bits): the one that drops it to zero completes the request.
+struct __align__(16) ServeTask {
+    unsigned long long tref;
+    int next_r, best_r, committed_r, lock, fail, pad;
+    uint8_t mu[64];
+    uint8_t rhop[64];
+};
+// A level's resident keys as the serving kernel reads them.
+struct ServeKeys {
+    const uint8_t *sk, *pk, *tr;
+    const int32_t *keys;
+    int n;
+};
+constexpr int SERVE_SIG_STRIDE = 4608;   // bytes per result signature (16-byte multiple >= 4595)
+struct ServeArgs {
+    ServeCtl *ctl;
+    const ServeReq *req;            // ring of R descriptors
+    const uint8_t *arena;           // message / signature bytes
+    ServeTask *tasks;               // ring of R records
+    int *worker_ticket;             // per worker: the Sign ticket it owns (-1: none), for helpers
+    int32_t *scratch;               // per worker: worker_polys polynomials
+    uint8_t *sig_stage;             // per worker: SERVE_SIG_STRIDE bytes (device)
+    int worker_polys;
+    int ring;                       // R, a power of two
+    ServeKeys keys[3];              // levels 2, 3, 5
+    uint8_t *sig_out;               // R x SERVE_SIG_STRIDE (host-mapped)
+    int32_t *status;                // R (host-mapped)
+    int32_t *iters;                 // R (host-mapped)
+    uint8_t *ok;                    // R (host-mapped)
+    unsigned long long *comp;       // completion ring, R entries (host-mapped)
+    int spec;                       // helpers per unfinished Sign (0: none)
+    int spin_limit;                 // polls of the commit lock
+    long long idle_ns;              // an idle worker exits after this long
+};
+// Polynomials of one serving worker's scratch (the largest level's keyed
+// Sign or keyed Verify scratch).
+size_t serve_worker_polys();
+// Resident workers of one serving launch (all SMs), capped by max_workers.
+cudaError_t serve_grid(int device, int max_workers, int &grid, int &workers);
+// Launches the serving kernel (grid from serve_grid) on s.
+cudaError_t launch_serve(const ServeArgs &a, int grid, cudaStream_t s);
+
 // test-only issue-rate probe (thread-ops per SM clock)
 cudaError_t measure_issue_rate(int op, double *rate);
 size_t split_state_bytes();

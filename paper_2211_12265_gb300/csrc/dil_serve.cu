@@ -1,0 +1,419 @@
+// Serving kernel: continuous batching on the device.
+//
+// One-warp workers stay resident and take requests from a device ring as the
+// host publishes them (the host copies a request's descriptor and bytes into
+// the ring, then its ticket count into ServeCtl::tail).  A free worker takes
+// the next ticket number with one atomicAdd on ServeCtl::head, published or
+// not, and serves it once the host has published it, so each request starts
+// as soon as its ticket is published (idle workers hold the next tickets) or
+// a busy worker frees up: there are no batch boundaries on the device.  Keys are resident (key store: A^, s^1,
+// s^2, t^0, NTT(t1 2^d), tr), so a Sign hashes only mu and rho' before its
+// rejection loop (Alg 2) and a Verify skips ExpandA and H(pk) (Alg 3).
+//
+// A worker whose ticket is not yet published helps an unfinished Sign
+// meanwhile (the dynamic scheduling of section 4.3, on the device), until its
+// ticket is published: it joins the request's record,
+// draws further repetition indices from the shared counter and evaluates
+// those nonces; the signature of the smallest accepting nonce is committed
+// under the record's lock, so results equal dil_sign's byte for byte.  The
+// record counts the workers holding it (owner and helpers, packed with the
+// ticket into one 64-bit word); the worker that drops the count to zero
+// writes the request's final status and its completion.  Nobody waits for
+// anybody: the only wait is the commit lock, bounded by spin_limit polls
+// (then the request fails with DIL_ETIMEOUT and the error word is set).
+//
+// Results go straight to mapped host memory: the signature and status (or
+// the accept byte), a system-scope fence, then the entry (completion number,
+// ticket) in the completion ring that the host polls.  Requests are read
+// through L2 only (their ring slots are rewritten while the kernel runs).
+// Workers exit when the host sets `stop` (the host stops an idle kernel)
+// unless their ticket is published, then they serve it first; a worker whose
+// ticket stays unpublished for idle_ns also exits and sets the error word.
+// Tickets taken but never published are abandoned at exit: the host sets
+// head back to its oldest uncompleted ticket before the next launch.
+#include <climits>
+#include <cstddef>
+
+#include "../../include/dil.h"
+#include "dil_kern.cuh"
+
+namespace dil {
+
+namespace {
+
+constexpr int SERVE_WARPS = 8;                 // warps (workers) per CTA
+constexpr unsigned NO_TICKET = 0xFFFFFFFFu;    // worker_ticket of a worker that owns no Sign
+constexpr int SCAN_CHUNKS = 4;                 // 32-entry chunks of worker_ticket an idle worker scans per pass
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire(const int *p) { return (int)ld_acquire(reinterpret_cast<const unsigned *>(p)); }
+__device__ __forceinline__ unsigned tail_of(const ServeArgs &a) {
+    return ld_acquire(reinterpret_cast<const unsigned *>(&a.ctl->tail));
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Appends ticket t to the completion ring (one thread; the request's results
+// are visible system-wide before this is called).
+__device__ __forceinline__ void complete(const ServeArgs &a, unsigned t) {
+    const unsigned c = atomicAdd(reinterpret_cast<unsigned *>(&a.ctl->comp), 1u);
+    volatile unsigned long long *e = a.comp + (c & (unsigned)(a.ring - 1));
+    *e = ((unsigned long long)c << 32) | t;
+}
+
+// Zeroes a result signature (the whole warp).
+__device__ __forceinline__ void zero_sig(uint8_t *sig, int lane) {
+    uint4 *q = reinterpret_cast<uint4 *>(sig);
+    for (int i = lane; i < SERVE_SIG_STRIDE / 16; i += 32) q[i] = make_uint4(0, 0, 0, 0);
+}
+
+// Final result of a Sign request, written by the last worker to leave its
+// record: status (and repetitions), a zeroed signature unless one was
+// committed, then the completion.
+template <int LEVEL>
+__device__ void finish_sign(const ServeArgs &a, unsigned t, ServeTask &tk, int lane) {
+    const int slot = (int)(t & (unsigned)(a.ring - 1));
+    const int fail = atomicOr(&tk.fail, 0);
+    const int committed = atomicOr(&tk.committed_r, 0);
+    const int status = fail ? DIL_ETIMEOUT : committed != INT_MAX ? DIL_OK : DIL_EITER;
+    if (status != DIL_OK) zero_sig(a.sig_out + (size_t)slot * SERVE_SIG_STRIDE, lane);
+    if (lane == 0) {
+        a.status[slot] = status;
+        a.iters[slot] = status == DIL_OK ? committed + 1 : status == DIL_EITER ? Lv<LEVEL>::MAX_ITER : 0;
+    }
+    __threadfence_system();
+    __syncwarp();
+    if (lane == 0) complete(a, t);
+}
+
+// Drops this worker's hold on record tk (ticket t); the last one out finishes
+// the request.
+template <int LEVEL>
+__device__ void leave(const ServeArgs &a, unsigned t, ServeTask &tk, int lane) {
+    __threadfence();
+    unsigned long long prev = 0;
+    if (lane == 0) prev = atomicAdd(&tk.tref, ~0ull);   // minus one
+    prev = __shfl_sync(FULL, prev, 0);
+    if ((prev & 0xFFFFFFFFull) == 1) finish_sign<LEVEL>(a, t, tk, lane);
+}
+
+// Commits the signature of accepting repetition r if it beats the committed one.
+// stage: the worker's SERVE_SIG_STRIDE-byte device buffer for the packed signature.
+template <int LEVEL>
+__device__ void commit(const ServeArgs &a, unsigned t, ServeTask &tk, int r, const int32_t *itr, GroupSmem &gs,
+                       uint8_t *stage, int lane) {
+    const int slot = (int)(t & (unsigned)(a.ring - 1));
+    int st = 0;
+    if (lane == 0) {
+        atomicMin(&tk.best_r, r);
+        int acquired = 0;
+        for (int i = 0; i < a.spin_limit; ++i) {
+            if (atomicCAS(&tk.lock, 0, 1) == 0) {
+                acquired = 1;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!acquired) {
+            atomicExch(&tk.fail, 1);
+            atomicExch(&a.ctl->error, DIL_ETIMEOUT);
+        }
+        __threadfence();
+        st = !acquired ? 0 : (r < atomicOr(&tk.committed_r, 0) && !atomicOr(&tk.fail, 0)) ? 2 : 1;
+    }
+    st = __shfl_sync(FULL, st, 0);
+    if (st == 2) {   // pack in device memory, then 16-byte stores to the mapped result
+        sign_pack<LEVEL, 1>(stage, itr, gs, 0, lane);
+        __syncwarp();
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.sig_out + (size_t)slot * SERVE_SIG_STRIDE);
+        for (int i = lane; i < (Lv<LEVEL>::SIG + 15) / 16; i += 32) dst[i] = src[i];
+    }
+    __threadfence_system();
+    __syncwarp();
+    if (lane == 0 && st >= 1) {
+        if (st == 2) atomicExch(&tk.committed_r, r);
+        __threadfence();
+        atomicExch(&tk.lock, 0);
+    }
+    __syncwarp();
+}
+
+// Draws repetitions of record tk until one accepts, the counter passes an
+// accepted one, the cap is reached or the request failed.  pre: the key's
+// precomputation; gs.hb (mu) and gs.rhop hold the message's hashes.  Two
+// consecutive repetitions per claim, so one mask-stream batch serves both.
+//
+// watch: a helper stops drawing repetitions once its own ticket `mine` is
+// published (it has a request to serve), but only between claims: a claimed
+// repetition below the best accepted one is always evaluated, else a larger
+// nonce than the smallest accepting one could be committed.
+template <int LEVEL>
+__device__ void repetitions(const ServeArgs &a, unsigned t, ServeTask &tk, const int32_t *pre, int32_t *itr,
+                            uint8_t *stage, GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt,
+                            int lane, bool watch = false, unsigned mine = 0) {
+    constexpr int PER_BATCH = Scratch<LEVEL>::MASK_BATCH / Lv<LEVEL>::L;
+    constexpr int CLAIM = PER_BATCH < 2 ? PER_BATCH : 2;
+    MaskStream ms{0, 0};
+    int next = 0, end = 0;
+    for (;;) {
+        int r = -1;
+        if (lane == 0) {
+            bool claim = true;
+            if (next >= end) {
+                if (watch && (int)(tail_of(a) - mine) > 0) {
+                    claim = false;
+                } else {
+                    next = atomicAdd(&tk.next_r, CLAIM);
+                    end = next + CLAIM;
+                }
+            }
+            if (claim) {
+                r = next++;
+                const int best = atomicOr(&tk.best_r, 0);
+                if (__ldcg(&tk.fail) || r >= Lv<LEVEL>::MAX_ITER || r >= best) r = -1;
+            }
+        }
+        r = __shfl_sync(FULL, r, 0);
+        if (r < 0) break;
+        if (sign_attempt<LEVEL, 1>(Lv<LEVEL>::L * r, pre, itr, ms, gs, ws, zt, izt, 0, 0, lane, &tk.best_r, r)) {
+            commit<LEVEL>(a, t, tk, r, itr, gs, stage, lane);
+            break;
+        }
+    }
+}
+
+// The request of ticket t as its owner: Verify to completion, or Sign:
+// prepare mu and rho', publish the record to helpers, repeat, leave.
+template <int LEVEL>
+__device__ void own(const ServeArgs &a, unsigned t, const ServeReq &rq, int worker, int32_t *mine, uint8_t *stage,
+                    GroupSmem &gs, WarpSmem &ws, const int32_t *zt, const int32_t *izt, int lane) {
+    using V = Lv<LEVEL>;
+    using S = Scratch<LEVEL>;
+    const int slot = (int)(t & (unsigned)(a.ring - 1));
+    const ServeKeys &ks = a.keys[LEVEL == 2 ? 0 : LEVEL == 3 ? 1 : 2];
+    const bool key_ok = rq.key >= 0 && rq.key < ks.n;
+    const uint8_t *msg = a.arena + rq.msg;
+    if (rq.op == 1) {   // Verify
+        int r = 0;
+        if (key_ok)
+            r = verify_task<LEVEL, 1, true>(ks.pk + (size_t)rq.key * V::PK, msg, (size_t)rq.mlen, a.arena + rq.sig,
+                                            mine, gs, ws, zt, izt, 0, 0, lane,
+                                            ks.keys + (size_t)rq.key * S::KEY_POLYS * N, ks.tr + (size_t)rq.key * 32);
+        if (lane == 0) a.ok[slot] = (uint8_t)r;
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) complete(a, t);
+        return;
+    }
+    if (!key_ok) {   // unknown key: rejected, not read
+        zero_sig(a.sig_out + (size_t)slot * SERVE_SIG_STRIDE, lane);
+        if (lane == 0) {
+            a.status[slot] = DIL_EINVAL;
+            a.iters[slot] = 0;
+        }
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) complete(a, t);
+        return;
+    }
+    ServeTask &tk = a.tasks[slot];
+    if (lane == 0) {
+        tk.next_r = 0;
+        tk.best_r = INT_MAX;
+        tk.committed_r = INT_MAX;
+        tk.lock = 0;
+        tk.fail = 0;
+        atomicExch(&tk.tref, ((unsigned long long)t << 32) | 1ull);   // held by the owner
+    }
+    sign_prepare_keyed<LEVEL, 1>(ks.sk + (size_t)rq.key * V::SK, msg, (size_t)rq.mlen, gs, 0, 0, lane);
+    tk.mu[lane] = gs.hb[HB_MU + lane];
+    tk.mu[32 + lane] = gs.hb[HB_MU + 32 + lane];
+    tk.rhop[lane] = gs.rhop[lane];
+    tk.rhop[32 + lane] = gs.rhop[32 + lane];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(&a.worker_ticket[worker], (int)t);
+    repetitions<LEVEL>(a, t, tk, ks.keys + (size_t)rq.key * S::KEY_POLYS * N, mine, stage, gs, ws, zt, izt, lane);
+    if (lane == 0) atomicExch(&a.worker_ticket[worker], (int)NO_TICKET);
+    leave<LEVEL>(a, t, tk, lane);
+}
+
+// Helps the Sign of ticket t (record already joined): its hashes from the
+// record, its key's precomputation from the store.
+template <int LEVEL>
+__device__ void help(const ServeArgs &a, unsigned t, const ServeReq &rq, int32_t *mine, uint8_t *stage, GroupSmem &gs,
+                     WarpSmem &ws, const int32_t *zt, const int32_t *izt, int lane, unsigned ticket) {
+    const int slot = (int)(t & (unsigned)(a.ring - 1));
+    ServeTask &tk = a.tasks[slot];
+    const ServeKeys &ks = a.keys[LEVEL == 2 ? 0 : LEVEL == 3 ? 1 : 2];
+    __threadfence();   // the owner wrote the hashes before it published the ticket
+    gs.hb[HB_MU + lane] = __ldcg(tk.mu + lane);
+    gs.hb[HB_MU + 32 + lane] = __ldcg(tk.mu + 32 + lane);
+    gs.rhop[lane] = __ldcg(tk.rhop + lane);
+    gs.rhop[32 + lane] = __ldcg(tk.rhop + 32 + lane);
+    __syncwarp();
+    repetitions<LEVEL>(a, t, tk, ks.keys + (size_t)rq.key * Scratch<LEVEL>::KEY_POLYS * N, mine, stage, gs, ws, zt,
+                       izt, lane, true, ticket);
+    leave<LEVEL>(a, t, tk, lane);
+}
+
+__device__ __forceinline__ ServeReq load_req(const ServeArgs &a, unsigned t) {
+    const ServeReq *p = a.req + (t & (unsigned)(a.ring - 1));
+    ServeReq r;
+    const int4 w0 = __ldcg(reinterpret_cast<const int4 *>(p));
+    const longlong2 w1 = __ldcg(reinterpret_cast<const longlong2 *>(p) + 1);
+    const long long w2 = __ldcg(reinterpret_cast<const long long *>(p) + 4);
+    r.op = w0.x;
+    r.level = w0.y;
+    r.key = w0.z;
+    r.pad = w0.w;
+    r.msg = (uint64_t)w1.x;
+    r.mlen = (uint64_t)w1.y;
+    r.sig = (uint64_t)w2;
+    return r;
+}
+
+// One pass over SCAN_CHUNKS x 32 entries of worker_ticket from *cursor for a
+// Sign that accepts another helper; joins it (CAS on its record) and
+// returns its ticket, or NO_TICKET.
+__device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned &cursor, int lane) {
+    unsigned found = NO_TICKET;
+#pragma unroll 1
+    for (int c = 0; c < SCAN_CHUNKS && found == NO_TICKET; ++c) {
+        const unsigned idx = (cursor + 32u * c + lane) % (unsigned)nworkers;
+        const unsigned u = (unsigned)__ldcg(a.worker_ticket + idx);
+        bool cand = false;
+        if (u != NO_TICKET) {
+            const ServeTask &tk = a.tasks[u & (unsigned)(a.ring - 1)];
+            const unsigned long long tr = __ldcg(&tk.tref);
+            cand = (unsigned)(tr >> 32) == u && (unsigned)tr > 0 && (unsigned)tr <= (unsigned)a.spec &&
+                   __ldcg(&tk.best_r) == INT_MAX;
+        }
+        const unsigned m = __ballot_sync(FULL, cand);
+        if (m) found = __shfl_sync(FULL, u, __ffs(m) - 1);
+    }
+    cursor += 32u * SCAN_CHUNKS;
+    if (found == NO_TICKET) return NO_TICKET;
+    int joined = 0;
+    if (lane == 0) {
+        ServeTask &tk = a.tasks[found & (unsigned)(a.ring - 1)];
+        unsigned long long cur = atomicAdd(&tk.tref, 0ull);
+        for (int tries = 0; tries < 8; ++tries) {
+            if ((unsigned)(cur >> 32) != found || (unsigned)cur == 0 || (unsigned)cur > (unsigned)a.spec) break;
+            const unsigned long long prev = atomicCAS(&tk.tref, cur, cur + 1);
+            if (prev == cur) {
+                joined = 1;
+                break;
+            }
+            cur = prev;
+        }
+    }
+    joined = __shfl_sync(FULL, joined, 0);
+    return joined ? found : NO_TICKET;
+}
+
+__global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const CtaView v = cta_setup<1>(smem);
+    GroupSmem &gs = *v.gs;
+    WarpSmem &ws = *v.ws;
+    const int lane = v.lane;
+    const int worker = blockIdx.x * v.groups + v.group;
+    const int nworkers = gridDim.x * v.groups;
+    int32_t *mine = a.scratch + (size_t)worker * a.worker_polys * N;
+    uint8_t *stage = a.sig_stage + (size_t)worker * SERVE_SIG_STRIDE;
+    unsigned cursor = (unsigned)worker * 2654435761u % (unsigned)nworkers;
+    unsigned ticket = 0;
+    bool holding = false;
+    long long waiting_since = -1;
+    for (;;) {
+        if (!holding) {   // take the next ticket number
+            unsigned t = 0;
+            if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned *>(&a.ctl->head), 1u);
+            ticket = __shfl_sync(FULL, t, 0);
+            holding = true;
+            waiting_since = -1;
+        }
+        int published = 0, stop = 0;
+        long long now = 0;
+        if (lane == 0) {
+            stop = ld_acquire(&a.ctl->stop);   // stop is written after every tail it follows
+            published = (int)(tail_of(a) - ticket) > 0;
+            now = global_ns();
+        }
+        published = __shfl_sync(FULL, published, 0);
+        if (published) {
+            holding = false;
+            const ServeReq rq = load_req(a, ticket);
+            switch (rq.level) {
+                case 2: own<2>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
+                case 3: own<3>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
+                default: own<5>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
+            }
+            continue;
+        }
+        if (__shfl_sync(FULL, stop, 0)) break;   // the ticket is abandoned: the host resets head
+        now = __shfl_sync(FULL, now, 0);
+        if (waiting_since < 0) waiting_since = now;
+        if (now - waiting_since > a.idle_ns) {   // bounded wait: record it and leave
+            if (lane == 0) atomicExch(&a.ctl->error, DIL_ETIMEOUT);
+            break;
+        }
+        // while the ticket is unpublished, help an unfinished Sign
+        const unsigned helped = a.spec > 0 ? find_and_join(a, nworkers, cursor, lane) : NO_TICKET;
+        if (helped != NO_TICKET) {
+            const ServeReq rq = load_req(a, helped);
+            switch (rq.level) {
+                case 2: help<2>(a, helped, rq, mine, stage, gs, ws, v.zt, v.izt, lane, ticket); break;
+                case 3: help<3>(a, helped, rq, mine, stage, gs, ws, v.zt, v.izt, lane, ticket); break;
+                default: help<5>(a, helped, rq, mine, stage, gs, ws, v.zt, v.izt, lane, ticket); break;
+            }
+            continue;
+        }
+        __nanosleep(500);
+    }
+}
+
+}  // namespace
+
+size_t serve_worker_polys() {
+    size_t m = 0;
+    const size_t v[] = {(size_t)Scratch<2>::ITR_POLYS, (size_t)Scratch<3>::ITR_POLYS, (size_t)Scratch<5>::ITR_POLYS,
+                        (size_t)Scratch<2>::KEYED_VERIFY_POLYS, (size_t)Scratch<3>::KEYED_VERIFY_POLYS,
+                        (size_t)Scratch<5>::KEYED_VERIFY_POLYS};
+    for (size_t x : v) m = x > m ? x : m;
+    return m;
+}
+
+cudaError_t serve_grid(int device, int max_workers, int &grid, int &workers) {
+    int sms = 0, occ = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    const size_t smem = cta_bytes(SERVE_WARPS, 1);
+    e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, SERVE_WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    grid = sms * occ;
+    if (max_workers > 0 && grid * SERVE_WARPS > max_workers) grid = max_workers / SERVE_WARPS;
+    if (grid < 1) grid = 1;
+    workers = grid * SERVE_WARPS;
+    return cudaSuccess;
+}
+
+cudaError_t launch_serve(const ServeArgs &a, int grid, cudaStream_t s) {
+    k_serve<<<grid, SERVE_WARPS * 32, cta_bytes(SERVE_WARPS, 1), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dil
