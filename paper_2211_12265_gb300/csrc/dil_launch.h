@@ -154,7 +154,8 @@ struct ServeCtl {
     int head;          // next ticket to claim
     int comp;          // completions issued (slots of the completion ring)
     int error;         // DIL_ETIMEOUT when a bounded wait ran out
-    int pad1[29];
+    int active;        // workers serving a request of their own ticket
+    int pad1[28];
     int stop;          // set by the host: workers exit once nothing is pending
     int pad2[31];
 };
@@ -192,6 +193,7 @@ struct ServeArgs {
     uint8_t *ok;                    // R (host-mapped)
     unsigned long long *comp;       // completion ring, R entries (host-mapped)
     int spec;                       // helpers per unfinished Sign (0: none)
+    int help_below;                 // a worker helps only while fewer than this many serve their own request
     int spin_limit;                 // polls of the commit lock
     long long idle_ns;              // an idle worker exits after this long
 };

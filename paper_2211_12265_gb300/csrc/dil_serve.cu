@@ -12,7 +12,9 @@
 //
 // A worker whose ticket is not yet published helps an unfinished Sign
 // meanwhile (the dynamic scheduling of section 4.3, on the device), until its
-// ticket is published: it joins the request's record,
+// ticket is published, as long as fewer than help_below workers serve
+// requests of their own (under load the speculative repetitions would take
+// issue slots from the requests on the same SMs): it joins the request's record,
 // draws further repetition indices from the shared counter and evaluates
 // those nonces; the signature of the smallest accepting nonce is committed
 // under the record's lock, so results equal dil_sign's byte for byte.  The
@@ -354,11 +356,13 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
         if (published) {
             holding = false;
             const ServeReq rq = load_req(a, ticket);
+            if (lane == 0) atomicAdd(&a.ctl->active, 1);
             switch (rq.level) {
                 case 2: own<2>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
                 case 3: own<3>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
                 default: own<5>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
             }
+            if (lane == 0) atomicSub(&a.ctl->active, 1);
             continue;
         }
         if (__shfl_sync(FULL, stop, 0)) break;   // the ticket is abandoned: the host resets head
@@ -368,8 +372,11 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
             if (lane == 0) atomicExch(&a.ctl->error, DIL_ETIMEOUT);
             break;
         }
-        // while the ticket is unpublished, help an unfinished Sign
-        const unsigned helped = a.spec > 0 ? find_and_join(a, nworkers, cursor, lane) : NO_TICKET;
+        // while the ticket is unpublished and the GPU is lightly loaded, help an unfinished Sign
+        int light = 0;
+        if (lane == 0) light = a.spec > 0 && ld_acquire(&a.ctl->active) < a.help_below;
+        light = __shfl_sync(FULL, light, 0);
+        const unsigned helped = light ? find_and_join(a, nworkers, cursor, lane) : NO_TICKET;
         if (helped != NO_TICKET) {
             const ServeReq rq = load_req(a, helped);
             switch (rq.level) {

@@ -608,6 +608,7 @@ bool ring_launch(dil_server *sv) {
               cudaHostGetDevicePointer((void **)&a.ok, g.m_ok, 0) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&a.comp, g.m_comp, 0) == cudaSuccess;
     a.spec = 8;
+    a.help_below = g.workers / 2;
     a.spin_limit = dil::PERSIST_SPIN_LIMIT;
     a.idle_ns = 10000000000ll;   // a ticket unpublished for 10 s (the host stops an idle kernel long before)
     ok = ok && cudaEventRecord(g.ev_pub, g.cstream) == cudaSuccess &&
