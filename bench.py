@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="level2")
     ap.add_argument("--n", type=int, default=0, help="override the task count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-served", action="store_true",
+                    help="leave out the served measurement (its kernel waits on copies made while it runs, which "
+                         "a profiler that serialises work would hold back)")
     return ap.parse_args()
 
 
@@ -344,7 +347,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     other_levels = {f"level{lv}": level_forms(ctx, lv, timed, stream, ranks, extra) for lv in (3, 5) if lv != level}
     mixed = mixed_forms(ctx, timed, stream, ranks, max(1, min(args.steps, 5)))
     ctx.apply_tuning()
-    served = served_measure(dev) if ranks.world == 1 else None
+    served = served_measure(dev) if ranks.world == 1 and not args.skip_served else None
 
     # e2e: host buffers through the host-form C entry points
     h_sk = torch.empty_like(sk, device="cpu").pin_memory()

@@ -176,6 +176,20 @@ struct ServeKeys {
     int n;
 };
 constexpr int SERVE_SIG_STRIDE = 4608;   // bytes per result signature (16-byte multiple >= 4595)
+// Request types (operation, level): 3 x op + level index (2, 3, 5 -> 0, 1, 2).
+constexpr int SERVE_TYPES = 6;
+constexpr int SERVE_MAX_SMS = 256;
+constexpr uint8_t SERVE_TYPE_ANY = 255;   // an SM without a home type
+// Forwarding queue of one request type: tickets claimed by workers of other
+// types' SMs, for the workers of SMs whose home type it is.  Entry i of its
+// ring holds (sequence << 32) | ticket; sequence p marks it free for the push
+// at position p, p + 1 marks it filled by that push.
+struct ServeFifo {
+    unsigned head;
+    unsigned pad0[31];
+    unsigned tail;
+    unsigned pad1[31];
+};
 struct ServeArgs {
     ServeCtl *ctl;
     const ServeReq *req;            // ring of R descriptors
@@ -194,6 +208,11 @@ struct ServeArgs {
     unsigned long long *comp;       // completion ring, R entries (host-mapped)
     int spec;                       // helpers per unfinished Sign (0: none)
     int help_below;                 // a worker helps only while fewer than this many serve their own request
+    ServeFifo *fifo;                // SERVE_TYPES forwarding queues
+    unsigned long long *fifo_ring;  // SERVE_TYPES x R entries
+    int type_sms[SERVE_TYPES];      // SMs whose home type it is (0: tickets of that type are not forwarded)
+    int fifo_limit;                 // forward to a queue only while it holds fewer than this per home SM
+    uint8_t sm_type[SERVE_MAX_SMS]; // home type of each SM (SERVE_TYPE_ANY: serves every type directly)
     int spin_limit;                 // polls of the commit lock
     long long idle_ns;              // an idle worker exits after this long
 };

@@ -28,6 +28,15 @@
 // the accept byte), a system-scope fence, then the entry (completion number,
 // ticket) in the completion ring that the host polls.  Requests are read
 // through L2 only (their ring slots are rewritten while the kernel runs).
+// Under load, every SM serves one request type (operation and level; the
+// host assigns the SMs in proportion to the recent work of each type): the
+// task bodies of different types thrash a shared instruction cache (a mix of
+// the three Sign levels on one SM measured 1.6x the warp time of one level).
+// A worker that claims a ticket of another type forwards it to that type's
+// queue and takes the next number; workers serve their own type's queue
+// before taking a number.  A ticket is served where it was claimed when its
+// type has no home SMs or a long queue, and at light load.
+//
 // Workers exit when the host sets `stop` (the host stops an idle kernel)
 // unless their ticket is published, then they serve it first; a worker whose
 // ticket stays unpublished for idle_ns also exits and sets the error word.
@@ -284,6 +293,46 @@ __device__ __forceinline__ ServeReq load_req(const ServeArgs &a, unsigned t) {
     return r;
 }
 
+__device__ __forceinline__ int type_of(const ServeReq &rq) {
+    return 3 * rq.op + (rq.level == 2 ? 0 : rq.level == 3 ? 1 : 2);
+}
+
+// Forwarding queues (lane 0 only).  A push reserves a position only when its
+// entry is free, so a failed push leaves nothing behind (the caller then
+// serves the ticket itself); a pop takes the head only when its entry is
+// filled.  Both give up after a few contended tries.
+__device__ bool fifo_push(const ServeArgs &a, int type, unsigned t) {
+    ServeFifo &f = a.fifo[type];
+    unsigned long long *ring = a.fifo_ring + (size_t)type * a.ring;
+    for (int tries = 0; tries < 16; ++tries) {
+        const unsigned pos = ld_acquire(&f.tail);
+        unsigned long long *e = ring + (pos & (unsigned)(a.ring - 1));
+        if ((unsigned)(atomicAdd(e, 0ull) >> 32) != pos) return false;   // entry still in use: full
+        if (atomicCAS(&f.tail, pos, pos + 1) == pos) {
+            atomicExch(e, ((unsigned long long)(pos + 1) << 32) | t);
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ bool fifo_pop(const ServeArgs &a, int type, unsigned &t) {
+    ServeFifo &f = a.fifo[type];
+    unsigned long long *ring = a.fifo_ring + (size_t)type * a.ring;
+    for (int tries = 0; tries < 16; ++tries) {
+        const unsigned pos = ld_acquire(&f.head);
+        unsigned long long *e = ring + (pos & (unsigned)(a.ring - 1));
+        const unsigned long long v = atomicAdd(e, 0ull);
+        if ((unsigned)(v >> 32) != pos + 1) return false;   // empty (or its push is still writing)
+        if (atomicCAS(&f.head, pos, pos + 1) == pos) {
+            atomicExch(e, (unsigned long long)(pos + (unsigned)a.ring) << 32);   // free for the push R later
+            t = (unsigned)v;
+            return true;
+        }
+    }
+    return false;
+}
+
 // One pass over SCAN_CHUNKS x 32 entries of worker_ticket from *cursor for a
 // Sign that accepts another helper; joins it (CAS on its record) and
 // returns its ticket, or NO_TICKET.
@@ -323,6 +372,25 @@ __device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned &cu
     return joined ? found : NO_TICKET;
 }
 
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
+// Serves ticket t as its owner, counted in ServeCtl::active.
+__device__ __forceinline__ void serve(const ServeArgs &a, unsigned t, const ServeReq &rq, int worker, int32_t *mine,
+                                      uint8_t *stage, GroupSmem &gs, WarpSmem &ws, const int32_t *zt,
+                                      const int32_t *izt, int lane) {
+    if (lane == 0) atomicAdd(&a.ctl->active, 1);
+    switch (rq.level) {
+        case 2: own<2>(a, t, rq, worker, mine, stage, gs, ws, zt, izt, lane); break;
+        case 3: own<3>(a, t, rq, worker, mine, stage, gs, ws, zt, izt, lane); break;
+        default: own<5>(a, t, rq, worker, mine, stage, gs, ws, zt, izt, lane); break;
+    }
+    if (lane == 0) atomicSub(&a.ctl->active, 1);
+}
+
 __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const CtaView v = cta_setup<1>(smem);
@@ -334,12 +402,25 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
     int32_t *mine = a.scratch + (size_t)worker * a.worker_polys * N;
     uint8_t *stage = a.sig_stage + (size_t)worker * SERVE_SIG_STRIDE;
     unsigned cursor = (unsigned)worker * 2654435761u % (unsigned)nworkers;
+    const unsigned smid = sm_id();
+    const int home = smid < SERVE_MAX_SMS ? a.sm_type[smid] : SERVE_TYPE_ANY;
     unsigned ticket = 0;
     bool holding = false;
     long long waiting_since = -1;
     for (;;) {
-        if (!holding) {   // take the next ticket number
-            unsigned t = 0;
+        if (!holding) {
+            if (home != SERVE_TYPE_ANY) {   // tickets of the home type forwarded from other SMs first
+                unsigned f = 0;
+                int got = 0;
+                if (lane == 0) got = fifo_pop(a, home, f);
+                got = __shfl_sync(FULL, got, 0);
+                f = __shfl_sync(FULL, f, 0);
+                if (got) {
+                    serve(a, f, load_req(a, f), worker, mine, stage, gs, ws, v.zt, v.izt, lane);
+                    continue;
+                }
+            }
+            unsigned t = 0;   // take the next ticket number
             if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned *>(&a.ctl->head), 1u);
             ticket = __shfl_sync(FULL, t, 0);
             holding = true;
@@ -356,13 +437,15 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
         if (published) {
             holding = false;
             const ServeReq rq = load_req(a, ticket);
-            if (lane == 0) atomicAdd(&a.ctl->active, 1);
-            switch (rq.level) {
-                case 2: own<2>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
-                case 3: own<3>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
-                default: own<5>(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane); break;
+            const int ty = type_of(rq);
+            int fwd = 0;   // under load, hand a ticket of another type to that type's SMs
+            if (lane == 0 && ty != home && a.type_sms[ty] > 0 && ld_acquire(&a.ctl->active) >= a.help_below) {
+                const ServeFifo &f = a.fifo[ty];
+                const unsigned len = ld_acquire(&f.tail) - ld_acquire(&f.head);
+                if (len < (unsigned)(a.fifo_limit * a.type_sms[ty])) fwd = fifo_push(a, ty, ticket);
             }
-            if (lane == 0) atomicSub(&a.ctl->active, 1);
+            if (__shfl_sync(FULL, fwd, 0)) continue;
+            serve(a, ticket, rq, worker, mine, stage, gs, ws, v.zt, v.izt, lane);
             continue;
         }
         if (__shfl_sync(FULL, stop, 0)) break;   // the ticket is abandoned: the host resets head

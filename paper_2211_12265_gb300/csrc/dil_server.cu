@@ -179,6 +179,11 @@ struct Ring {
     int *d_worker_ticket = nullptr;
     int32_t *d_scratch = nullptr;
     uint8_t *d_sig_stage = nullptr;     // per worker: a signature packed before it goes to mapped memory
+    dil::ServeFifo *d_fifo = nullptr;   // forwarding queues by request type
+    unsigned long long *d_fifo_ring = nullptr;
+    unsigned long long *h_fifo_init = nullptr;   // pinned: the queues' entries as every launch starts them
+    int sms = 0;
+    double type_work[dil::SERVE_TYPES] = {};    // recent warp time per request type (publisher), for the SM shares
     dil::ServeReq *h_req = nullptr;     // pinned staging of the descriptors
     uint8_t *h_arena = nullptr;         // pinned staging of the arena
     unsigned *h_words = nullptr;        // pinned sources of the tail / stop copies
@@ -215,6 +220,11 @@ constexpr unsigned RING_WORDS = 4096;   // h_words entries (two halves, reused a
 // the host stages the rest.
 constexpr size_t RING_CHUNK = 1024, RING_CHUNK_BYTES = (size_t)4 << 20;
 constexpr double RING_IDLE_STOP_S = 0.002;   // the host stops a kernel idle this long
+constexpr int RING_FIFO_PER_SM = 16;          // forwarding stops while a queue holds this many per home SM
+// Warp time of one request by type in microseconds (GB300, 32 of 32 warps per
+// SM busy: Sign 2 / 3 / 5, Verify 2 / 3 / 5), plus the hash of its message.
+constexpr double RING_TYPE_US[dil::SERVE_TYPES] = {720, 1030, 1110, 80, 94, 122};
+constexpr double RING_MSG_US_PER_BYTE = 0.05;
 
 struct Group {
     int op, level, first, count;
@@ -470,6 +480,7 @@ void ring_free(Ring &g) {
     if (g.cstream) cudaStreamSynchronize(g.cstream);
     cudaFree(g.d_ctl); cudaFree(g.d_req); cudaFree(g.d_arena); cudaFree(g.d_tasks);
     cudaFree(g.d_worker_ticket); cudaFree(g.d_scratch); cudaFree(g.d_sig_stage);
+    cudaFree(g.d_fifo); cudaFree(g.d_fifo_ring); cudaFreeHost(g.h_fifo_init);
     cudaFreeHost(g.h_req); cudaFreeHost(g.h_arena); cudaFreeHost(g.h_words);
     cudaFreeHost(g.m_sig); cudaFreeHost(g.m_status); cudaFreeHost(g.m_iters); cudaFreeHost(g.m_ok);
     cudaFreeHost(g.m_comp);
@@ -514,6 +525,9 @@ bool ring_alloc(Ring &g, int device, size_t budget, size_t msg_cap) {
               cudaMalloc(&g.d_worker_ticket, (size_t)g.workers * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&g.d_scratch, (size_t)g.workers * per_worker) == cudaSuccess &&
               cudaMalloc(&g.d_sig_stage, (size_t)g.workers * dil::SERVE_SIG_STRIDE) == cudaSuccess &&
+              cudaMalloc(&g.d_fifo, dil::SERVE_TYPES * sizeof(dil::ServeFifo)) == cudaSuccess &&
+              cudaMalloc(&g.d_fifo_ring, dil::SERVE_TYPES * R * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMallocHost(&g.h_fifo_init, dil::SERVE_TYPES * R * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&g.h_req, R * sizeof(dil::ServeReq)) == cudaSuccess &&
               cudaMallocHost(&g.h_arena, arena) == cudaSuccess &&
               cudaMallocHost(&g.h_words, RING_WORDS * sizeof(unsigned)) == cudaSuccess &&
@@ -529,6 +543,10 @@ bool ring_alloc(Ring &g, int device, size_t budget, size_t msg_cap) {
         // completion entry i first expects completion number i: start every
         // entry at a number it cannot hold then
         for (size_t i = 0; ok && i < R; ++i) g.m_comp[i] = (unsigned long long)(unsigned)(i - R) << 32;
+        // forwarding entry i is free for the push at position i
+        for (size_t ty = 0; ok && ty < (size_t)dil::SERVE_TYPES; ++ty)
+            for (size_t i = 0; i < R; ++i) g.h_fifo_init[ty * R + i] = (unsigned long long)i << 32;
+        ok = ok && cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
@@ -565,6 +583,47 @@ bool ring_copy_word(Ring &g, unsigned *dst, unsigned value) {
 bool kernel_running(Ring &g) { return g.launched && cudaEventQuery(g.kdone) == cudaErrorNotReady; }
 
 size_t ring_poll(dil_server *sv, bool fail_all = false);
+
+// Home request type of each SM, in proportion to the recent warp time of each
+// type (largest remainders; a type with work gets at least one SM); no
+// recent work: every SM serves every type.  The history halves per launch.
+void assign_home_types(Ring &g, dil::ServeArgs &a) {
+    for (int s = 0; s < dil::SERVE_MAX_SMS; ++s) a.sm_type[s] = dil::SERVE_TYPE_ANY;
+    for (int ty = 0; ty < dil::SERVE_TYPES; ++ty) a.type_sms[ty] = 0;
+    double total = 0;
+    for (double w : g.type_work) total += w;
+    const int sms = std::min(g.sms, dil::SERVE_MAX_SMS);
+    int active_types = 0;
+    for (double w : g.type_work) active_types += w > 0;
+    if (total <= 0 || sms < active_types) return;
+    int given = 0;
+    double rem[dil::SERVE_TYPES];
+    for (int ty = 0; ty < dil::SERVE_TYPES; ++ty) {
+        const double share = g.type_work[ty] / total * sms;
+        a.type_sms[ty] = g.type_work[ty] > 0 ? std::max(1, (int)share) : 0;
+        rem[ty] = share - a.type_sms[ty];
+        given += a.type_sms[ty];
+    }
+    while (given < sms) {   // largest remainders
+        int best = -1;
+        for (int ty = 0; ty < dil::SERVE_TYPES; ++ty)
+            if (g.type_work[ty] > 0 && (best < 0 || rem[ty] > rem[best])) best = ty;
+        a.type_sms[best]++;
+        rem[best] -= 1;
+        ++given;
+    }
+    while (given > sms) {   // the at-least-one rule overshot: take from the largest
+        int big = 0;
+        for (int ty = 1; ty < dil::SERVE_TYPES; ++ty)
+            if (a.type_sms[ty] > a.type_sms[big]) big = ty;
+        a.type_sms[big]--;
+        --given;
+    }
+    int s = 0;
+    for (int ty = 0; ty < dil::SERVE_TYPES; ++ty)
+        for (int k = 0; k < a.type_sms[ty]; ++k) a.sm_type[s++] = (uint8_t)ty;
+    for (double &w : g.type_work) w *= 0.5;
+}
 
 // Launches the serving kernel on the resident keys (after the copies issued
 // so far).  The previous launch has exited: every ticket it served is
@@ -609,6 +668,15 @@ bool ring_launch(dil_server *sv) {
               cudaHostGetDevicePointer((void **)&a.comp, g.m_comp, 0) == cudaSuccess;
     a.spec = 8;
     a.help_below = g.workers / 2;
+    // forwarding queues start empty (a ticket left in one by the previous
+    // launch is uncompleted and is claimed again through head)
+    ok = ok && cudaMemsetAsync(g.d_fifo, 0, dil::SERVE_TYPES * sizeof(dil::ServeFifo), g.cstream) == cudaSuccess &&
+         cudaMemcpyAsync(g.d_fifo_ring, g.h_fifo_init, dil::SERVE_TYPES * (size_t)g.R * sizeof(unsigned long long),
+                         cudaMemcpyHostToDevice, g.cstream) == cudaSuccess;
+    a.fifo = g.d_fifo;
+    a.fifo_ring = g.d_fifo_ring;
+    a.fifo_limit = RING_FIFO_PER_SM;
+    assign_home_types(g, a);
     a.spin_limit = dil::PERSIST_SPIN_LIMIT;
     a.idle_ns = 10000000000ll;   // a ticket unpublished for 10 s (the host stops an idle kernel long before)
     ok = ok && cudaEventRecord(g.ev_pub, g.cstream) == cudaSuccess &&
@@ -787,6 +855,9 @@ bool ring_publish(dil_server *sv) {
         const int slot = (int)((t0 + i) & mask);
         g.slot_aend[slot].store(starts[i] + req_bytes(batch[i]), std::memory_order_relaxed);
         g.slot_req[slot].store(batch[i], std::memory_order_release);
+        const Req *r = batch[i];
+        const int ty = 3 * r->op + level_slot(r->level);
+        g.type_work[ty] += RING_TYPE_US[ty] + RING_MSG_US_PER_BYTE * (double)r->mlen;
     }
     bool ok = true;
     auto h2d = [&](void *dst, const void *src, size_t n) {
