@@ -336,7 +336,7 @@ __device__ bool fifo_pop(const ServeArgs &a, int type, unsigned &t) {
 // One pass over SCAN_CHUNKS x 32 entries of worker_ticket from *cursor for a
 // Sign that accepts another helper; joins it (CAS on its record) and
 // returns its ticket, or NO_TICKET.
-__device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned &cursor, int lane) {
+__device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned spec, unsigned &cursor, int lane) {
     unsigned found = NO_TICKET;
 #pragma unroll 1
     for (int c = 0; c < SCAN_CHUNKS && found == NO_TICKET; ++c) {
@@ -346,7 +346,7 @@ __device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned &cu
         if (u != NO_TICKET) {
             const ServeTask &tk = a.tasks[u & (unsigned)(a.ring - 1)];
             const unsigned long long tr = __ldcg(&tk.tref);
-            cand = (unsigned)(tr >> 32) == u && (unsigned)tr > 0 && (unsigned)tr <= (unsigned)a.spec &&
+            cand = (unsigned)(tr >> 32) == u && (unsigned)tr > 0 && (unsigned)tr <= spec &&
                    __ldcg(&tk.best_r) == INT_MAX;
         }
         const unsigned m = __ballot_sync(FULL, cand);
@@ -359,7 +359,7 @@ __device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned &cu
         ServeTask &tk = a.tasks[found & (unsigned)(a.ring - 1)];
         unsigned long long cur = atomicAdd(&tk.tref, 0ull);
         for (int tries = 0; tries < 8; ++tries) {
-            if ((unsigned)(cur >> 32) != found || (unsigned)cur == 0 || (unsigned)cur > (unsigned)a.spec) break;
+            if ((unsigned)(cur >> 32) != found || (unsigned)cur == 0 || (unsigned)cur > spec) break;
             const unsigned long long prev = atomicCAS(&tk.tref, cur, cur + 1);
             if (prev == cur) {
                 joined = 1;
@@ -455,11 +455,16 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
             if (lane == 0) atomicExch(&a.ctl->error, DIL_ETIMEOUT);
             break;
         }
-        // while the ticket is unpublished and the GPU is lightly loaded, help an unfinished Sign
-        int light = 0;
-        if (lane == 0) light = a.spec > 0 && ld_acquire(&a.ctl->active) < a.help_below;
-        light = __shfl_sync(FULL, light, 0);
-        const unsigned helped = light ? find_and_join(a, nworkers, cursor, lane) : NO_TICKET;
+        // while the ticket is unpublished, help an unfinished Sign: up to spec
+        // helpers per Sign while fewer than help_below workers serve their own
+        // request, a quarter of that up to 3/2 help_below, none above
+        unsigned spec_now = 0;
+        if (lane == 0) {
+            const int act = ld_acquire(&a.ctl->active);
+            spec_now = act < a.help_below ? a.spec : 2 * act < 3 * a.help_below ? (a.spec + 3) / 4 : 0;
+        }
+        spec_now = __shfl_sync(FULL, spec_now, 0);
+        const unsigned helped = spec_now ? find_and_join(a, nworkers, spec_now, cursor, lane) : NO_TICKET;
         if (helped != NO_TICKET) {
             const ServeReq rq = load_req(a, helped);
             switch (rq.level) {
