@@ -548,12 +548,16 @@ def mixed_forms(ctx, timed, stream, ranks, steps: int, n: int = 100000) -> dict:
 
 def plain_replay(dev: int, keys: dict, req: dict, reps: int = 5) -> dict:
     """The requests of a served trace run by the plain kernels, one launch per
-    (operation, level) with the whole trace resident on the device: the
-    plain one-launch-per-batch form at its largest batch."""
+    (operation, level) over the whole trace: the plain one-launch-per-batch
+    form at its largest batch.  Timed twice: with the requests resident on
+    the device, and with what a service moves per request inside the timed
+    region (messages and signatures to verify in from pinned host memory,
+    signatures and results out; keys resident, as for the server)."""
     import torch
 
     from paper_2211_12265_gb300 import dil
     groups = []
+    stream = torch.cuda.current_stream()
     with dil.Context(dev) as ctx:
         ctx.apply_tuning()
         for op in (0, 1):
@@ -564,43 +568,66 @@ def plain_replay(dev: int, keys: dict, req: dict, reps: int = 5) -> dict:
                 parts = [req["msg"][req["msg_off"][i]:req["msg_off"][i + 1]] for i in idx]
                 o = np.zeros(idx.size + 1, dtype=np.uint64)
                 o[1:] = np.cumsum([p.size for p in parts])
-                m = torch.from_numpy(np.concatenate(parts + [np.zeros(1, np.uint8)])).cuda()
-                o = torch.from_numpy(o).cuda()
+                g = {"op": op, "lv": lv, "k": idx.size,
+                     "h_msg": torch.from_numpy(np.concatenate(parts + [np.zeros(1, np.uint8)])).pin_memory(),
+                     "h_off": torch.from_numpy(o).pin_memory()}
+                g["msg"] = g["h_msg"].cuda()
+                g["off"] = g["h_off"].cuda()
                 kidx = req["key"][idx]
                 sigb = dil.SIZES[lv][2]
                 if op == 0:
-                    sk = torch.from_numpy(np.ascontiguousarray(keys[lv][1][kidx])).cuda()
-                    sig = torch.empty((idx.size, sigb), dtype=torch.uint8, device="cuda")
-                    st = torch.empty(idx.size, dtype=torch.int32, device="cuda")
-                    groups.append(("sign", lv, idx.size, lambda lv=lv, sk=sk, m=m, o=o, sig=sig, st=st, k=idx.size:
-                                   dil.dil_sign(ctx.handle, lv, k, sk, m, o, sig, st)))
+                    g["key"] = torch.from_numpy(np.ascontiguousarray(keys[lv][1][kidx])).cuda()
+                    g["out"] = torch.empty((idx.size, sigb), dtype=torch.uint8, device="cuda")
+                    g["st"] = torch.empty(idx.size, dtype=torch.int32, device="cuda")
+                    g["h_out"] = torch.empty((idx.size, sigb), dtype=torch.uint8).pin_memory()
+                    g["h_st"] = torch.empty(idx.size, dtype=torch.int32).pin_memory()
                 else:
-                    pk = torch.from_numpy(np.ascontiguousarray(keys[lv][0][kidx])).cuda()
-                    sg = torch.from_numpy(np.ascontiguousarray(req["sig_in"][idx, :sigb])).cuda()
-                    ok = torch.empty(idx.size, dtype=torch.uint8, device="cuda")
-                    groups.append(("verify", lv, idx.size, lambda lv=lv, pk=pk, m=m, o=o, sg=sg, ok=ok, k=idx.size:
-                                   dil.dil_verify(ctx.handle, lv, k, pk, m, o, sg, ok)))
+                    g["key"] = torch.from_numpy(np.ascontiguousarray(keys[lv][0][kidx])).cuda()
+                    g["h_sig"] = torch.from_numpy(np.ascontiguousarray(req["sig_in"][idx, :sigb])).pin_memory()
+                    g["sig"] = g["h_sig"].cuda()
+                    g["out"] = torch.empty(idx.size, dtype=torch.uint8, device="cuda")
+                    g["h_out"] = torch.empty(idx.size, dtype=torch.uint8).pin_memory()
+                groups.append(g)
 
-        def run():
+        def run(copies: bool):
             for g in groups:
-                g[3]()
-        run()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            run()
-            e1.record()
+                if copies:
+                    g["msg"].copy_(g["h_msg"], non_blocking=True)
+                    g["off"].copy_(g["h_off"], non_blocking=True)
+                    if g["op"] == 1:
+                        g["sig"].copy_(g["h_sig"], non_blocking=True)
+                if g["op"] == 0:
+                    dil.dil_sign(ctx.handle, g["lv"], g["k"], g["key"], g["msg"], g["off"], g["out"], g["st"], stream)
+                else:
+                    dil.dil_verify(ctx.handle, g["lv"], g["k"], g["key"], g["msg"], g["off"], g["sig"], g["out"],
+                                   stream)
+                if copies:
+                    g["h_out"].copy_(g["out"], non_blocking=True)
+                    if g["op"] == 0:
+                        g["h_st"].copy_(g["st"], non_blocking=True)
+
+        def timed(copies: bool) -> float:
+            run(copies)
             torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-    t = float(np.median(ts))
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run(copies)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+        t_dev = timed(False)
+        t_e2e = timed(True)
     n = int(req["op"].size)
-    return {"ops_s": n / (t * 1e-3), "ms": t, "requests": n, "launches": len(groups),
-            "form": "plain kernels, one launch per (operation, level), inputs resident on the device"}
+    return {"ops_s": n / (t_dev * 1e-3), "ms": t_dev, "e2e_ops_s": n / (t_e2e * 1e-3), "e2e_ms": t_e2e,
+            "requests": n, "launches": len(groups),
+            "form": "plain kernels, one launch per (operation, level); ops_s with the requests resident on the "
+                    "device, e2e_ops_s with messages / signatures copied in and results copied out"}
 
 
-def served_measure(dev: int, n: int = 40000, fractions=SERVED_FRACTIONS) -> dict:
+def served_measure(dev: int, n: int = 80000, fractions=SERVED_FRACTIONS) -> dict:
     """Config 5: the served mix on the continuous-batching server: saturated
     ops/s, an arrival-rate sweep with p50/p99, and at each rate the best p99
     of static batching over STATIC_GRID; beside it the plain kernels' rate on
@@ -641,6 +668,7 @@ def served_measure(dev: int, n: int = 40000, fractions=SERVED_FRACTIONS) -> dict
                             "max_wait_s": sorted({g[1] for g in STATIC_GRID})},
             "plain_kernels_same_requests": plain,
             "served_over_plain": sat["ops_s"] / plain["ops_s"],
+            "served_over_plain_e2e": sat["ops_s"] / plain["e2e_ops_s"],
             "server_batches": batches, "server_requests": carried, "server_launches": launches}
 
 

@@ -12,9 +12,9 @@
 //
 // A worker whose ticket is not yet published helps an unfinished Sign
 // meanwhile (the dynamic scheduling of section 4.3, on the device), until its
-// ticket is published, as long as fewer than help_below workers serve
-// requests of their own (under load the speculative repetitions would take
-// issue slots from the requests on the same SMs): it joins the request's record,
+// ticket is published, with fewer helpers as more workers serve requests of
+// their own (under load the speculative repetitions would take issue slots
+// from the requests on the same SMs): it joins the request's record,
 // draws further repetition indices from the shared counter and evaluates
 // those nonces; the signature of the smallest accepting nonce is committed
 // under the record's lock, so results equal dil_sign's byte for byte.  The
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
             const ServeReq rq = load_req(a, ticket);
             const int ty = type_of(rq);
             int fwd = 0;   // under load, hand a ticket of another type to that type's SMs
-            if (lane == 0 && ty != home && a.type_sms[ty] > 0 && ld_acquire(&a.ctl->active) >= a.help_below) {
+            if (lane == 0 && ty != home && a.type_sms[ty] > 0 && ld_acquire(&a.ctl->active) >= a.forward_above) {
                 const ServeFifo &f = a.fifo[ty];
                 const unsigned len = ld_acquire(&f.tail) - ld_acquire(&f.head);
                 if (len < (unsigned)(a.fifo_limit * a.type_sms[ty])) fwd = fifo_push(a, ty, ticket);
@@ -457,11 +457,11 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
         }
         // while the ticket is unpublished, help an unfinished Sign: up to spec
         // helpers per Sign while fewer than help_below workers serve their own
-        // request, a quarter of that up to 3/2 help_below, none above
+        // request, a quarter of that up to help_until, none above
         unsigned spec_now = 0;
         if (lane == 0) {
             const int act = ld_acquire(&a.ctl->active);
-            spec_now = act < a.help_below ? a.spec : 2 * act < 3 * a.help_below ? (a.spec + 3) / 4 : 0;
+            spec_now = act < a.help_below ? a.spec : act < a.help_until ? (a.spec + 3) / 4 : 0;
         }
         spec_now = __shfl_sync(FULL, spec_now, 0);
         const unsigned helped = spec_now ? find_and_join(a, nworkers, spec_now, cursor, lane) : NO_TICKET;

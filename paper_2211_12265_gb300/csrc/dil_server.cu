@@ -667,7 +667,9 @@ bool ring_launch(dil_server *sv) {
               cudaHostGetDevicePointer((void **)&a.ok, g.m_ok, 0) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&a.comp, g.m_comp, 0) == cudaSuccess;
     a.spec = 8;
-    a.help_below = g.workers / 2;
+    a.help_below = g.workers * 35 / 100;
+    a.help_until = g.workers * 8 / 10;
+    a.forward_above = g.workers / 2;
     // forwarding queues start empty (a ticket left in one by the previous
     // launch is uncompleted and is claimed again through head)
     ok = ok && cudaMemsetAsync(g.d_fifo, 0, dil::SERVE_TYPES * sizeof(dil::ServeFifo), g.cstream) == cudaSuccess &&
