@@ -34,8 +34,9 @@ class Server:
         self.close()
 
     def set_batching(self, min_batch: int = 1, max_wait_s: float = 0.0) -> None:
-        """Continuous batching by default; min_batch / max_wait_s > 0 make the
-        dispatcher batch statically (see dil_server_set_batching)."""
+        """Continuous batching on the device when max_wait_s is 0 (the
+        default); max_wait_s > 0 selects static batching, where a batch starts
+        with min_batch pending requests or once the oldest waited max_wait_s."""
         dil.dil_server_set_batching(self.handle, min_batch, max_wait_s)
 
     def set_tuning(self, op: int, level: int, warps_per_cta: int, warps_per_task: int) -> None:

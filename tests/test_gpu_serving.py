@@ -219,9 +219,10 @@ def test_server_alone_and_in_the_mix(keys, orc):
 
 
 def test_server_policies_and_shapes_agree(keys, orc):
-    """Static batching, continuous batching and other launch shapes of the
-    keyed kernels give byte-identical results on the same arrival trace, each
-    equal to the oracle's."""
+    """Continuous batching (the serving kernel), static batching (the keyed
+    kernels) and static batching with other launch shapes of the keyed kernels
+    give byte-identical results on the same arrival trace, each equal to the
+    oracle's."""
     from paper_2211_12265_gb300 import dil, serving
     req, exp = oracle_trace(orc, keys, 200, 5e5, seed=305, hi=4000)
     with serving.Server(0, memory_budget=512 << 20, streams=2, max_batch=128) as srv:
@@ -230,16 +231,17 @@ def test_server_policies_and_shapes_agree(keys, orc):
         base = srv.replay(req)
         srv.set_batching(64, 0.002)
         static = srv.replay(req)
-        srv.set_batching(1, 0.0)
-        for lv in keys:
+        for lv in keys:                            # the shapes apply to the static path's keyed kernels
             srv.set_tuning(0, lv, 2, 1)
             srv.set_tuning(1, lv, 8, 2)
         shaped = srv.replay(req)
+        srv.set_batching(1, 0.0)
+        again = srv.replay(req)
         with pytest.raises(dil.DilError):
             srv.set_tuning(0, 2, 6, 4)             # 4 does not divide 6
         with pytest.raises(dil.DilError):
             srv.set_batching(0, 0.0)
-    for out in (base, static, shaped):
+    for out in (base, static, shaped, again):
         assert_matches_oracle(req, out, exp)
 
 
