@@ -246,7 +246,10 @@ typedef struct {
  * (0 = 4 GiB, key stores excluded) is split in two: the slots' device buffers
  * must fit one half (max_batch is halved until they do; DIL_ENOMEM if even 1
  * does not fit), the request ring, arena and serving workers are sized to the
- * other (fewer workers when it is small). */
+ * other (fewer workers when it is small).  Of that half the message arena
+ * takes a quarter, at most 1 GiB, and the ring a slot per 2 KiB of arena, at
+ * most 131072 slots.  The host side mirrors the ring in pinned memory: the
+ * arena's size again, plus 4.7 KB of mapped result space per slot. */
 int dil_server_create(int device, size_t memory_budget, int streams, int max_batch, dil_server **out);
 /* Stops the dispatcher after in-flight work, frees everything.  NULL accepted. */
 int dil_server_destroy(dil_server *srv);

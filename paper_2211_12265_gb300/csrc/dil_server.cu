@@ -219,6 +219,8 @@ constexpr unsigned RING_WORDS = 4096;   // h_words entries (two halves, reused a
 // Largest publication: the first requests of a burst reach the device while
 // the host stages the rest.
 constexpr size_t RING_CHUNK = 1024, RING_CHUNK_BYTES = (size_t)4 << 20;
+constexpr size_t RING_ARENA_MAX = (size_t)1 << 30;   // message arena, bytes
+constexpr size_t RING_SLOTS_MAX = (size_t)1 << 17;   // R: request slots, mapped result slots
 constexpr double RING_IDLE_STOP_S = 0.002;   // the host stops a kernel idle this long
 constexpr int RING_FIFO_PER_SM = 16;          // forwarding stops while a queue holds this many per home SM
 // Warp time of one request by type in microseconds (GB300, 32 of 32 warps per
@@ -495,15 +497,23 @@ void ring_free(Ring &g) {
 }
 
 // Sizes the ring from its share of the memory budget: the arena takes a
-// quarter (at most 256 MiB, at least two of the largest requests), the
+// quarter (at most RING_ARENA_MAX, at least two of the largest requests), the
 // descriptors and records an eighth at most, the workers' scratch the rest.
+//
+// Tickets are published in order and a slot (and its arena bytes) frees only
+// when every older request has completed, so one long Sign holds back
+// publishing once R tickets or `arena` bytes lie beyond it.  A Sign with 30
+// repetitions runs about 20 ms under full load, some 80,000 requests at the
+// saturated rate: the ring gets a slot per 2 KB of arena (the serving mix's
+// requests take 2.6 KB of message and, for Verify, a signature), up to
+// RING_SLOTS_MAX.
 bool ring_alloc(Ring &g, int device, size_t budget, size_t msg_cap) {
     const size_t big = msg_cap + MAX_SIG + 64;
-    size_t arena = std::min<size_t>(budget / 4, (size_t)256 << 20);
+    size_t arena = std::min<size_t>(budget / 4, RING_ARENA_MAX);
     arena = std::max(arena, 2 * big);
     arena = (arena + 4095) & ~(size_t)4095;
-    size_t R = pow2_floor(std::max<size_t>(budget / 8 / (sizeof(dil::ServeReq) + sizeof(dil::ServeTask)), 64));
-    R = std::min<size_t>(R, 32768);
+    size_t R = std::min<size_t>(budget / 8 / (sizeof(dil::ServeReq) + sizeof(dil::ServeTask)), arena / 2048);
+    R = std::min<size_t>(pow2_floor(std::max<size_t>(R, 64)), RING_SLOTS_MAX);
     const size_t per_worker = dil::serve_worker_polys() * POLY;
     const size_t used = arena + R * (sizeof(dil::ServeReq) + sizeof(dil::ServeTask));
     const size_t left = budget > used ? budget - used : 0;
