@@ -207,8 +207,7 @@ struct ServeArgs {
     uint8_t *ok;                    // R (host-mapped)
     unsigned long long *comp;       // completion ring, R entries (host-mapped)
     int spec;                       // helpers per unfinished Sign (0: none)
-    int help_below;                 // all spec helpers while fewer than this many workers serve their own request
-    int help_until;                 // a quarter of them below this many, none above
+    int help_below;                 // spec helpers while fewer than this many workers serve their own request, none above
     int forward_above;              // tickets are forwarded to their type's SMs from this many on
     ServeFifo *fifo;                // SERVE_TYPES forwarding queues
     unsigned long long *fifo_ring;  // SERVE_TYPES x R entries

@@ -12,9 +12,9 @@
 //
 // A worker whose ticket is not yet published helps an unfinished Sign
 // meanwhile (the dynamic scheduling of section 4.3, on the device), until its
-// ticket is published, with fewer helpers as more workers serve requests of
-// their own (under load the speculative repetitions would take issue slots
-// from the requests on the same SMs): it joins the request's record,
+// ticket is published, only while few workers serve requests of their own
+// (under load the speculative repetitions would take issue slots from the
+// requests on the same SMs): it joins the request's record,
 // draws further repetition indices from the shared counter and evaluates
 // those nonces; the signature of the smallest accepting nonce is committed
 // under the record's lock, so results equal dil_sign's byte for byte.  The
@@ -457,12 +457,9 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
         }
         // while the ticket is unpublished, help an unfinished Sign: up to spec
         // helpers per Sign while fewer than help_below workers serve their own
-        // request, a quarter of that up to help_until, none above
+        // request, none above
         unsigned spec_now = 0;
-        if (lane == 0) {
-            const int act = ld_acquire(&a.ctl->active);
-            spec_now = act < a.help_below ? a.spec : act < a.help_until ? (a.spec + 3) / 4 : 0;
-        }
+        if (lane == 0) spec_now = ld_acquire(&a.ctl->active) < a.help_below ? a.spec : 0;
         spec_now = __shfl_sync(FULL, spec_now, 0);
         const unsigned helped = spec_now ? find_and_join(a, nworkers, spec_now, cursor, lane) : NO_TICKET;
         if (helped != NO_TICKET) {
