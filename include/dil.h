@@ -101,6 +101,38 @@ int dil_sign_ex(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint
 int dil_verify(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
                const uint64_t *msg_off, const uint8_t *sig, uint8_t *ok, void *stream);
 
+/* ----------------------------------------------------------------------------
+ * Caller-owned A^.  The matrix A^ = ExpandA(rho) (Alg 4; Alg 1 samples it in
+ * the NTT domain, Alg 2 and Alg 3 use it) depends only on a key's rho, so a
+ * caller that signs or verifies many batches under the same keys can expand
+ * it once and pass it in.  Layout of one key's A^: k x l polynomials of 256
+ * uint32 words, polynomial (i, j) at index i l + j, coefficient m at word m
+ * (the NTT-domain evaluation order that ExpandA samples), each in [0, q).
+ * A batch's A^ array holds task i's matrix at ahat + i k l 256 (device
+ * memory, 16-byte aligned, owned by the caller).  See also the key store
+ * below, which keeps the other per-key precomputation resident as well.
+ * ------------------------------------------------------------------------- */
+
+/* A^ = ExpandA(rho) for n keys: task i's 32-byte rho at rho + i rho_stride
+ * (rho_stride >= 32; pass a public-key array with rho_stride = PK bytes, since
+ * pk starts with rho) into ahat (n x k l x 256 uint32).  DIL_EINVAL for a bad
+ * level, stride, NULL pointer or a misaligned ahat. */
+int dil_expand_a(dil_ctx *ctx, int level, size_t n, const uint8_t *rho, size_t rho_stride, uint32_t *ahat,
+                 void *stream);
+
+/* dil_sign_ex with task i's A^ read from ahat instead of expanded from the rho
+ * in its secret key; ahat NULL is dil_sign_ex.  The library does not check
+ * that ahat matches the keys: an A^ of another rho gives signatures that do
+ * not verify.  Runs one warp per task (warps per CTA from the Sign tuning). */
+int dil_sign_a(dil_ctx *ctx, int level, size_t n, const uint8_t *sk, const uint8_t *msg,
+               const uint64_t *msg_off, const uint32_t *ahat, uint8_t *sig, int32_t *task_status,
+               int32_t *iterations, void *stream);
+
+/* dil_verify with task i's A^ read from ahat (NULL: dil_verify).  t1 and
+ * tr = H(pk) still come from pk, so a wrong A^ rejects. */
+int dil_verify_a(dil_ctx *ctx, int level, size_t n, const uint8_t *pk, const uint8_t *msg,
+                 const uint64_t *msg_off, const uint8_t *sig, const uint32_t *ahat, uint8_t *ok, void *stream);
+
 /* Sign that allocates no memory (the paper has no counterpart).  For callers
  * that cannot call cudaMalloc while signing: a service whose device memory is
  * already owned by its own allocator, a latency-critical path that cannot

@@ -270,6 +270,84 @@ int dil_verify(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t
     return DIL_OK;
 }
 
+// ---------------------------------------------------------------- caller-owned A^
+namespace {
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+size_t ahat_words(int level) {
+    const int k = level == 2 ? 4 : level == 3 ? 6 : 8, l = level == 2 ? 4 : level == 3 ? 5 : 7;
+    return (size_t)k * l * 256;
+}
+}  // namespace
+
+int dil_expand_a(dil_ctx *c, int level, size_t n, const uint8_t *rho, size_t rho_stride, uint32_t *ahat,
+                 void *stream) {
+    TraceRange trace("dil_expand_a");
+    if (!c || !level_ok(level) || rho_stride < 32) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!rho || !ahat || !aligned16(ahat) || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    cudaError_t e = dil::launch_expand_a(level, (int)n, rho, rho_stride, reinterpret_cast<int32_t *>(ahat),
+                                         c->warps[2][lidx(level)], (cudaStream_t)stream);
+    return e != cudaSuccess ? cuda_fail(e) : DIL_OK;
+}
+
+int dil_sign_a(dil_ctx *c, int level, size_t n, const uint8_t *sk, const uint8_t *msg, const uint64_t *msg_off,
+               const uint32_t *ahat, uint8_t *sig, int32_t *task_status, int32_t *iterations, void *stream) {
+    if (!ahat) return dil_sign_ex(c, level, n, sk, msg, msg_off, sig, task_status, iterations, stream);
+    TraceRange trace("dil_sign_a");
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!sk || !msg_off || !sig || !aligned16(ahat) || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    const int l = level == 2 ? 4 : level == 3 ? 5 : 7;
+    const int cap = (65536 - l) / l + 1;
+    const int max_iter = (c->max_iter > 0 && c->max_iter < cap) ? c->max_iter : cap;
+    const size_t chunk = chunk_tasks(c, dil::OP_SIGN, level, n);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * dil::scratch_polys(dil::OP_SIGN, level) * POLY_BYTES);
+    if (rc) return rc;
+    const int32_t *a = reinterpret_cast<const int32_t *>(ahat);
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        const int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_sign_a(level, m, sk + skb * s0, msg, msg_off + s0, a + ahat_words(level) * s0,
+                                           sig + sigb * s0, task_status ? task_status + s0 : nullptr,
+                                           iterations ? iterations + s0 : nullptr, (int32_t *)c->ws, max_iter,
+                                           c->warps[1][lidx(level)], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
+int dil_verify_a(dil_ctx *c, int level, size_t n, const uint8_t *pk, const uint8_t *msg, const uint64_t *msg_off,
+                 const uint8_t *sig, const uint32_t *ahat, uint8_t *ok, void *stream) {
+    if (!ahat) return dil_verify(c, level, n, pk, msg, msg_off, sig, ok, stream);
+    TraceRange trace("dil_verify_a");
+    if (!c || !level_ok(level)) return DIL_EINVAL;
+    if (n == 0) return DIL_OK;
+    if (!pk || !msg_off || !sig || !ok || !aligned16(ahat) || n > (size_t)INT32_MAX) return DIL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    size_t pkb, skb, sigb;
+    sizes_of(level, pkb, skb, sigb);
+    const size_t chunk = chunk_tasks(c, dil::OP_VERIFY, level, n);
+    if (chunk == 0) return DIL_ENOMEM;
+    int rc = ensure_ws(c, chunk * dil::scratch_polys(dil::OP_VERIFY, level) * POLY_BYTES);
+    if (rc) return rc;
+    const int32_t *a = reinterpret_cast<const int32_t *>(ahat);
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        const int m = (int)std::min(chunk, n - s0);
+        cudaError_t e = dil::launch_verify_a(level, m, pk + pkb * s0, msg, msg_off + s0, sig + sigb * s0,
+                                             a + ahat_words(level) * s0, ok + s0, (int32_t *)c->ws,
+                                             c->warps[2][lidx(level)], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DIL_OK;
+}
+
 // ---------------------------------------------------------------- persistent
 int dil_set_persistent_tuning(dil_ctx *c, int warps_per_cta, int warps_per_task, int ctas_per_sm, int chunk,
                               int speculation) {

@@ -37,6 +37,19 @@ cudaError_t launch_verify(int level, int n, const uint8_t *pk, const uint8_t *ms
 // tasks (its code and local-memory reservation are in place afterwards).
 cudaError_t warm_sign(int level, int warps, int p, cudaStream_t s);
 
+// Resident-A^ forms (one warp per task, `warps` warps per CTA): A^ of n keys
+// from rho (task i's 32 bytes at rho + i rho_stride) into ahat (n x k l x 256
+// words, 16-byte aligned); Sign and Verify with task i's A^ at
+// ahat + i k l 256 instead of ExpandA.
+cudaError_t launch_expand_a(int level, int n, const uint8_t *rho, size_t rho_stride, int32_t *ahat, int warps,
+                            cudaStream_t s);
+cudaError_t launch_sign_a(int level, int n, const uint8_t *sk, const uint8_t *msg, const uint64_t *off,
+                          const int32_t *ahat, uint8_t *sig, int32_t *status, int32_t *iters, int32_t *scratch,
+                          int max_iter, int warps, cudaStream_t s);
+cudaError_t launch_verify_a(int level, int n, const uint8_t *pk, const uint8_t *msg, const uint64_t *off,
+                            const uint8_t *sig, const int32_t *ahat, uint8_t *ok, int32_t *scratch, int warps,
+                            cudaStream_t s);
+
 // resident keys: per-key polynomials (A^, s^1, s^2, t^0, NTT(t1 2^d)) and
 // per-task scratch of a keyed Sign (y, y^, w, z)
 size_t key_polys(int level);

@@ -482,11 +482,22 @@ __device__ void gen_task(const uint8_t *__restrict__ seed, uint8_t *pk, uint8_t 
 // Alg 2: Sign
 // -------------------------------------------------------------------------
 
+// Copies polynomials [lo, hi) of src (a caller's A^, 256 words each) to dst
+// with 16-byte loads and stores.
+__device__ __forceinline__ void copy_polys(const int32_t *__restrict__ src, int lo, int hi, int32_t *dst, int lane) {
+    const int4 *q = reinterpret_cast<const int4 *>(src + lo * N);
+    int4 *d = reinterpret_cast<int4 *>(dst + lo * N);
+#pragma unroll 2
+    for (int i = lane; i < (hi - lo) * (N / 4); i += 32) d[i] = __ldg(q + i);
+}
+
 // Precomputation shared by every repetition: mu, rho', A^, s^1, s^2, t^0.
-template <int LEVEL, int P>
+// AHAT: A^ is the caller's (ahat_in: k l polynomials, ExpandA(rho) of the
+// task's key) and is copied instead of sampled.
+template <int LEVEL, int P, bool AHAT = false>
 __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__restrict__ msg, size_t mlen,
                              int32_t *scratch, GroupSmem &gs, WarpSmem &ws, const int32_t *zt, int g, int bar,
-                             int lane) {
+                             int lane, const int32_t *__restrict__ ahat_in = nullptr) {
     using V = Lv<LEVEL>;
     using S = Scratch<LEVEL>;
     int32_t r[8];
@@ -511,7 +522,10 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
     }
     // A^ = ExpandA(rho)
     constexpr int KL = V::K * V::L;
-    expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, ws, lane);
+    if constexpr (AHAT)
+        copy_polys(ahat_in, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, lane);
+    else
+        expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + S::AH * N, ws, lane);
     // s^1, s^2, t^0: polynomials u = 0 .. l + 2k - 1 across the group
 #pragma unroll 1
     for (int u = g; u < V::L + 2 * V::K; u += P) {
@@ -802,7 +816,9 @@ __device__ void sign_zero(uint8_t *sig, int g, int lane) {
 // -------------------------------------------------------------------------
 // KEYED: the public key is resident; `key` holds its A^ and NTT(t1 2^d)
 // (KEY_POLYS layout) and `tr` its H(pk), so neither is recomputed.
-template <int LEVEL, int P, bool KEYED = false>
+// AHAT: `key` is the caller's A^ of this key (k l polynomials, ExpandA(rho));
+// t1 and H(pk) come from pk as in the plain form.
+template <int LEVEL, int P, bool KEYED = false, bool AHAT = false>
 __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__restrict__ msg, size_t mlen,
                            const uint8_t *__restrict__ sig, int32_t *scratch, GroupSmem &gs, WarpSmem &ws,
                            const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
@@ -860,11 +876,11 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     // warp with more than one sixteen-state batch of A^ carries H(pk) in the
     // batches' spare instance.
     constexpr int KL = V::K * V::L;
-    constexpr bool RIDE = P == 1 && !KEYED && KL > K16_STATES;
+    constexpr bool RIDE = P == 1 && !KEYED && !AHAT && KL > K16_STATES;
     if constexpr (RIDE) {
         K16Rider rider(pk, V::PK, reinterpret_cast<uint32_t *>(gs.tr));
         expand_a_range<LEVEL>(gs.rho, 0, KL, scratch + V::L * N, ws, lane, rider);
-    } else if (!KEYED) {
+    } else if (!KEYED && !AHAT) {
         expand_a_range<LEVEL>(gs.rho, share_lo<KL, P>(g), share_lo<KL, P>(g + 1), scratch + V::L * N, ws, lane);
     }
     // mu = H(H(rho || t1) || M), on the last warp
@@ -888,7 +904,7 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
     challenge_hat<LEVEL>(ch, gs.ctilde, ws, zt, lane);
     // v = INTT(A^ o z^ - c^ o NTT(t1 2^d)); w1' = UseHint(h, v)
     using S = Scratch<LEVEL>;
-    const int32_t *ahat = KEYED ? key + S::AH * N : scratch + V::L * N;
+    const int32_t *ahat = KEYED ? key + S::AH * N : AHAT ? key : scratch + V::L * N;
 #pragma unroll 1
     for (int i = g; i < V::K; i += P) {
         accumulate_row(acc, ahat + i * V::L * N, V::L, scratch, lane);

@@ -57,6 +57,9 @@ def load() -> ctypes.CDLL:
                 "dil_sign_ex": [P, I, S, P, P, P, P, P, P, P],
                 "dil_verify": [P, I, S, P, P, P, P, P, P],
                 "dil_sign_noalloc": [I, S, P, P, P, P, P, P],
+                "dil_expand_a": [P, I, S, P, S, P, P],
+                "dil_sign_a": [P, I, S, P, P, P, P, P, P, P, P],
+                "dil_verify_a": [P, I, S, P, P, P, P, P, P, P],
                 "dil_keygen_host": [P, I, S, P, P, P, P],
                 "dil_sign_host": [P, I, S, P, P, P, P, P, P],
                 "dil_verify_host": [P, I, S, P, P, P, P, P, P],
@@ -182,6 +185,24 @@ def dil_sign_ex(ctx, level, n, sk, msg, msg_off, sig, task_status=None, iteratio
 def dil_verify(ctx, level, n, pk, msg, msg_off, sig, ok, stream=None):
     return _check(load().dil_verify(ctx, level, n, _ptr(pk), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(ok),
                                     _stream(stream)), "dil_verify")
+
+
+def dil_expand_a(ctx, level, n, rho, rho_stride, ahat, stream=None):
+    """A^ = ExpandA(rho) of n keys into ahat (n x k x l x 256 words)."""
+    return _check(load().dil_expand_a(ctx, level, n, _ptr(rho), rho_stride, _ptr(ahat), _stream(stream)),
+                  "dil_expand_a")
+
+
+def dil_sign_a(ctx, level, n, sk, msg, msg_off, ahat, sig, task_status=None, iterations=None, stream=None):
+    """dil_sign_ex with each task's A^ taken from ahat (None: dil_sign_ex)."""
+    return _check(load().dil_sign_a(ctx, level, n, _ptr(sk), _ptr(msg), _ptr(msg_off), _ptr(ahat), _ptr(sig),
+                                    _ptr(task_status), _ptr(iterations), _stream(stream)), "dil_sign_a")
+
+
+def dil_verify_a(ctx, level, n, pk, msg, msg_off, sig, ahat, ok, stream=None):
+    """dil_verify with each task's A^ taken from ahat (None: dil_verify)."""
+    return _check(load().dil_verify_a(ctx, level, n, _ptr(pk), _ptr(msg), _ptr(msg_off), _ptr(sig), _ptr(ahat),
+                                      _ptr(ok), _stream(stream)), "dil_verify_a")
 
 
 def dil_sign_noalloc(level, n, sk, msg, msg_off, sig, task_status=None, stream=None):
