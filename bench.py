@@ -12,7 +12,9 @@ host-buffer C entry points with the copies inside the timed region.
 The same line carries every other benchmark configuration, each measured
 in the same run:
   * ``forms``: the persistent form of Sign on the same batch (device work
-    queue, speculative nonces, CUDA graph), the split-kernel ablation, and
+    queue, speculative nonces, CUDA graph), the split-kernel ablation,
+    ``caller_ahat``: Sign and Verify of the batch reading the keys' A^ from
+    dil_expand_a (and that expansion's rate), and
     ``level3`` / ``level5``: Dilithium3 and Dilithium5, 10,000 tasks each with
     messages of 32..4096 bytes, plain and persistent Sign, Verify, KeyGen;
     ``mixed_200k``: persistent Sign of 100,000 Dilithium2 + 100,000
@@ -344,6 +346,22 @@ def run_ours(args, ranks: Ranks) -> dict | None:
     # the other configurations, each in its own launch configuration
     timed = _timer(torch, flush, stream, ranks)
     extra = max(1, min(args.steps, 10))
+    # caller-owned A^: expanded once per key (timed alone), then Sign and
+    # Verify of the same batch reading it instead of sampling it
+    kl = {2: 16, 3: 30, 5: 56}[level]
+    ahat = torch.empty((n, kl * 256), dtype=torch.int32, device="cuda")
+    t_exp = timed(lambda: dil.dil_expand_a(ctx.handle, level, n, pk, pk.shape[1], ahat, stream), extra)
+    sig_a = torch.empty_like(sig)
+    st_a = torch.empty_like(status)
+    ok_a = torch.empty(n, dtype=torch.uint8, device="cuda")
+    t_sign_a = timed(lambda: dil.dil_sign_a(ctx.handle, level, n, sk, msg, off, ahat, sig_a, st_a, stream=stream), extra)
+    t_ver_a = timed(lambda: dil.dil_verify_a(ctx.handle, level, n, pk, msg, off, sig, ahat, ok_a, stream), extra)
+    assert bool(torch.equal(sig_a, sig)) and bool((st_a == 0).all()) and bool(ok_a.all())
+    ahat_forms = {"expand_a_keys_s": ranks.world * n / (t_exp * 1e-3),
+                  "sign_ops_s": ranks.world * n / (t_sign_a * 1e-3),
+                  "verify_ops_s": ranks.world * n / (t_ver_a * 1e-3),
+                  "note": "dil_sign_a / dil_verify_a with the keys' A^ from dil_expand_a (one warp per task)"}
+    del ahat
     other_levels = {f"level{lv}": level_forms(ctx, lv, timed, stream, ranks, extra) for lv in (3, 5) if lv != level}
     mixed = mixed_forms(ctx, timed, stream, ranks, max(1, min(args.steps, 5)))
     ctx.apply_tuning()
@@ -420,7 +438,7 @@ def run_ours(args, ranks: Ranks) -> dict | None:
                   "persistent_sign_ms": p_sign_ms,
                   "split_sign_ops_s": ranks.world * n / (s_sign_ms * 1e-3), "split_sign_rounds": rounds,
                   "split_note": "fusion ablation: precompute kernel + two kernels per repetition round",
-                  **other_levels, "mixed_200k": mixed},
+                  "caller_ahat": ahat_forms, **other_levels, "mixed_200k": mixed},
         "served": served,
         "breakdown": {"sign_ops_s": ranks.world * n / (ranks.max(sign_mean_ms) * 1e-3),
                       "verify_ops_s": ranks.world * n / (ranks.max(float(np.mean(ver_ms))) * 1e-3),
