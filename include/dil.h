@@ -249,7 +249,8 @@ int dil_verify_keyed(dil_ctx *ctx, const dil_keystore *ks, size_t n, const int32
  *     arriving requests into the ring and publishes them; the kernel's
  *     one-warp workers take each request as soon as one is free (no batch
  *     boundaries on the device), idle workers help unfinished Signs with
- *     further nonces (the smallest accepting one is committed), and results
+ *     further nonces while few workers are busy (the smallest accepting one
+ *     is committed), under load each SM serves one request type, and results
  *     are written to mapped host memory and handed back as they complete.
  *     The kernel exits after a few idle milliseconds and is relaunched when
  *     requests arrive;
