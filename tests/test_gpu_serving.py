@@ -282,3 +282,65 @@ def test_server_cancel_pending_requests(keys, orc):
             assert status == dil.ECANCELED
         else:
             assert status == dil.OK and sig == ref[i].tobytes()
+
+
+@pytest.mark.parametrize("policy", ["continuous", "static"])
+def test_server_edge_lengths_and_unknown_keys(keys, orc, policy):
+    """Messages of 0 and 1 bytes, around the block edges of mu = H(tr || M)
+    (tr is 32 bytes and SHAKE256's rate 136, so M of 103..105 and 239..241
+    bytes) and of the server's maximum length, at all levels and for both
+    operations, equal the oracle's results; requests naming a key outside the
+    store are answered with DIL_EINVAL and a zero signature (Sign) or a reject
+    (Verify)."""
+    from paper_2211_12265_gb300 import serving
+    with serving.Server(0, memory_budget=512 << 20, streams=2, max_batch=256) as srv:
+        for lv in keys:
+            srv.add_keys(lv, *keys[lv])
+        cap = min(int(srv.msg_capacity), 16384)
+        edge = [0, 1, 103, 104, 105, 239, 240, 241, cap]
+        ops, lvls, lens = [], [], []
+        for lv in LEVELS:
+            for op in (0, 1):
+                for m in edge:
+                    ops.append(op)
+                    lvls.append(lv)
+                    lens.append(m)
+        n = len(ops)
+        op = np.array(ops, dtype=np.int32)
+        level = np.array(lvls, dtype=np.int32)
+        lens = np.array(lens, dtype=np.int64)
+        key = np.random.default_rng(7).integers(0, N_KEYS, n).astype(np.int32)
+        bad = np.zeros(n, dtype=bool)
+        bad[5::7] = True                                     # some of each operation and level
+        key[bad] = np.where(np.arange(n)[bad] % 2 == 0, N_KEYS, -1)
+        msg, off = W.messages(lens, 91)
+        sig_in = np.zeros((n, SIG_STRIDE), dtype=np.uint8)
+        exp_sig = np.zeros((n, SIG_STRIDE), dtype=np.uint8)
+        exp_status = np.zeros(n, dtype=np.int32)
+        exp_ok = np.zeros(n, dtype=np.uint8)
+        for lv in LEVELS:
+            sigb = _sig_layout(lv)[0]
+            for o in (0, 1):
+                idx = np.nonzero((level == lv) & (op == o) & ~bad)[0]
+                m, mo = _gather(msg, off, idx)
+                s, st, _ = orc.sign_batch(lv, keys[lv][1][key[idx]], m, mo)
+                if o == 0:
+                    exp_sig[idx, :sigb] = s
+                    exp_status[idx] = st
+                else:
+                    sig_in[idx, :sigb] = s
+                    exp_ok[idx] = orc.verify_batch(lv, keys[lv][0][key[idx]], m, mo, s)
+        exp_status[bad & (op == 0)] = -1                     # DIL_EINVAL
+        assert exp_ok[(op == 1) & ~bad].all()
+        req = {"arrival": np.zeros(n), "op": op, "level": level, "key": key, "msg": msg, "msg_off": off,
+               "sig_in": sig_in}
+        if policy == "static":
+            srv.set_batching(16, 0.002)
+        out = srv.replay(req)
+    sign = op == 0
+    assert np.array_equal(out["status"][sign], exp_status[sign])
+    for i in np.nonzero(sign)[0]:
+        sigb = _sig_layout(int(level[i]))[0]
+        assert np.array_equal(out["sig"][i, :sigb], exp_sig[i, :sigb]), f"request {i} (len {lens[i]})"
+    assert np.array_equal(out["ok"][~sign], exp_ok[~sign])
+    assert bad[sign].any() and bad[~sign].any()
