@@ -72,6 +72,7 @@ L2_FLUSH_BYTES = 512 << 20
 # static batching (the plain one-launch-per-batch service): grid searched per arrival rate
 STATIC_GRID = [(mb, w) for mb in (128, 512, 2048) for w in (0.0005, 0.002, 0.008)]
 SERVED_FRACTIONS = (0.25, 0.5, 0.75, 0.9)
+SERVED_REPLAYS = 3   # continuous batching: median of this many replays of each trace
 
 WORKLOADS = {
     "level2": dict(level=2, n=10000, config=2),
@@ -657,12 +658,19 @@ def served_measure(dev: int, n: int = 80000, fractions=SERVED_FRACTIONS) -> dict
             srv.add_keys(lv, *keys[lv])
         srv.replay(serving.serving_workload(keys, n, rate=1e9, seed=100))         # warm-up (host buffers touched)
         sat_req = serving.serving_workload(keys, n, rate=1e9, seed=101)
-        sat = serving.summarize(sat_req, srv.replay(sat_req))
+
+        def median_of(req, key, runs=SERVED_REPLAYS):
+            # the replay with the median `key` of `runs` replays of one trace
+            rs = sorted((serving.summarize(req, srv.replay(req)) for _ in range(runs)), key=lambda r: r[key])
+            out = dict(rs[len(rs) // 2])
+            out["replays"] = runs
+            return out
+        sat = median_of(sat_req, "ops_s")
         rows, static_rows = [], []
         for i, f in enumerate(fractions):
             rq = serving.serving_workload(keys, n, rate=f * sat["ops_s"], seed=102 + i)
             srv.set_batching(1, 0.0)
-            r = serving.summarize(rq, srv.replay(rq))
+            r = median_of(rq, "p99_ms")
             r["offered_fraction"] = f
             rows.append(r)
             best = None
