@@ -120,7 +120,7 @@ def summarize(req: dict, out: dict) -> dict:
     lat = out["latency"]
     return {"requests": int(req["op"].size), "ops_s": req["op"].size / out["wall"],
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "wall_s": out["wall"]}
+            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3), "wall_s": out["wall"]}
 
 
 def sweep(server: Server, keys: dict, rates, n_per_rate: int = 20000, seed: int = 11) -> list:
