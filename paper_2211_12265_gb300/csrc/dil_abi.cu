@@ -287,6 +287,8 @@ int dil_expand_a(dil_ctx *c, int level, size_t n, const uint8_t *rho, size_t rho
     if (!rho || !ahat || !aligned16(ahat) || n > (size_t)INT32_MAX) return DIL_EINVAL;
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
+    // one warp per key, in the CTA size of Verify's tuning (the other kernel
+    // whose first step is ExpandA); the output needs no workspace
     cudaError_t e = dil::launch_expand_a(level, (int)n, rho, rho_stride, reinterpret_cast<int32_t *>(ahat),
                                          c->warps[2][lidx(level)], (cudaStream_t)stream);
     return e != cudaSuccess ? cuda_fail(e) : DIL_OK;
