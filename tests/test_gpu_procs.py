@@ -93,6 +93,51 @@ def test_verify_rejections_match_oracle(ctx, orc, level):
     assert ok[::reps].all() and ok.sum() == 16
 
 
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_verify_rejects_noncanonical_hints(ctx, orc, level):
+    """Two encodings of a valid signature's own hint set that a lenient
+    decoder would accept (c~ still matches): a nonzero byte in an unused
+    index slot, and two indices of one polynomial swapped.  The strict
+    decoding of the round-3 hint encoding rejects both, on the GPU exactly as
+    in the oracle; the unmodified signatures verify."""
+    from gpu_util import gpu_verify
+    p = orc.params(level)
+    omega, k = p["omega"], p["k"]
+    seeds, msg, off = _batch(orc, level, 48, 5)
+    pk, sk = orc.keygen_batch(level, seeds)
+    sig, _, _ = orc.sign_batch(level, sk, msg, off)
+    hoff = sig.shape[1] - omega - k
+    rows, kinds = [], []
+    for i in range(sig.shape[0]):
+        h = sig[i, hoff:]
+        counts = [int(c) for c in h[omega:]]
+        if counts[-1] < omega:                                  # an unused index slot exists
+            t = sig[i].copy()
+            t[hoff + counts[-1]] = 1 + (i % 200)
+            rows.append((i, t))
+            kinds.append("unused")
+        prev = 0
+        for c in counts:                                        # a polynomial with two or more hints
+            if c - prev >= 2:
+                t = sig[i].copy()
+                t[hoff + prev], t[hoff + prev + 1] = t[hoff + prev + 1], t[hoff + prev]
+                rows.append((i, t))
+                kinds.append("order")
+                break
+            prev = c
+    assert "unused" in kinds and "order" in kinds
+    idx = np.array([r[0] for r in rows])
+    S = np.stack([r[1] for r in rows])
+    P = pk[idx]
+    M = np.concatenate([msg[off[i]:off[i + 1]] for i in idx])
+    O = np.zeros(idx.size + 1, dtype=np.uint64)
+    O[1:] = np.cumsum([int(off[i + 1] - off[i]) for i in idx])
+    want = orc.verify_batch(level, P, M, O, S)
+    assert not want.any()                                       # the oracle decodes strictly
+    assert not gpu_verify(ctx, level, P, M, O, S).any()
+    assert gpu_verify(ctx, level, pk, msg, off, sig).all()
+
+
 def test_empty_and_single(ctx, orc):
     import torch
     from gpu_util import dev, gpu_keygen, gpu_sign, gpu_verify
@@ -110,13 +155,16 @@ def test_empty_and_single(ctx, orc):
     assert gpu_verify(ctx, level, pk, msg, off, sig)[0] == 1
 
 
-@pytest.mark.parametrize("level", [2, 5])
+@pytest.mark.parametrize("level", [2, 3, 5])
 def test_long_and_empty_messages(ctx, orc, level):
     """Messages of 0 bytes, exactly one and two SHAKE256 blocks around the mu
     hash's boundaries, and 64 KB / 1 MB, mixed in one batch: signatures equal
-    the oracle's and all verify; a flipped byte at the end of the longest
-    message is rejected."""
-    from gpu_util import gpu_keygen, gpu_sign, gpu_verify
+    the oracle's in the plain, persistent and caller-owned A^ forms and all
+    verify (also with the caller's A^); a flipped byte at the end of the
+    longest message is rejected."""
+    import torch
+    from gpu_util import dev, gpu_keygen, gpu_sign, gpu_verify, host
+    from paper_2211_12265_gb300 import dil
     lens = np.array([0, 1, 72, 103, 104, 135, 136, 239, 240, 65536, 1 << 20, 0, 5], dtype=np.int64)
     n = lens.size
     rng = np.random.default_rng(31)
@@ -133,6 +181,24 @@ def test_long_and_empty_messages(ctx, orc, level):
     bad[int(off[11]) - 1] ^= 0x80                       # last byte of the 1 MB message
     ok = gpu_verify(ctx, level, pk, bad, off, sig)
     assert not ok[10] and ok[:10].all() and ok[11:].all()
+    # the persistent form and the caller-owned A^ forms on the same batch
+    d_sk, d_pk, d_msg, d_off = dev(sk), dev(pk), dev(msg), dev(off)
+    psig = torch.full((n, sig.shape[1]), 0x5A, dtype=torch.uint8, device="cuda")
+    pst = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    dil.dil_sign_persistent(ctx.handle, [dil.sign_job(level, n, d_sk, d_msg, d_off, psig, pst)])
+    k, l = {2: (4, 4), 3: (6, 5), 5: (8, 7)}[level]
+    ahat = torch.empty((n, k * l * 256), dtype=torch.int32, device="cuda")
+    dil.dil_expand_a(ctx.handle, level, n, d_pk, pk.shape[1], ahat)
+    asig = torch.zeros_like(psig)
+    ast = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    dil.dil_sign_a(ctx.handle, level, n, d_sk, d_msg, d_off, ahat, asig, ast)
+    aok = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    dil.dil_verify_a(ctx.handle, level, n, d_pk, dev(bad), d_off, dev(sig), ahat, aok)
+    torch.cuda.synchronize()
+    assert dil.dil_persistent_status(ctx.handle) == dil.OK
+    assert np.array_equal(host(psig), osig) and (host(pst) == 0).all()
+    assert np.array_equal(host(asig), osig) and (host(ast) == 0).all()
+    assert np.array_equal(host(aok), ok)
 
 
 def test_iteration_cap(ctx, orc):

@@ -91,6 +91,44 @@ def test_sampled_bit_flips_rejected(orc, level):
     assert orc.verify(level, pk, m, sig)
 
 
+@pytest.mark.parametrize("level", [2, 3, 5])
+def test_noncanonical_hint_encodings_rejected(orc, level):
+    """Strict hint decoding: re-encodings of a valid signature's own hint set
+    (a nonzero byte in an unused index slot; two indices of one polynomial
+    swapped) leave c~ matching, so only the decoding rules reject them.  The
+    oracle rejects every one and accepts the originals."""
+    p = orc.params(level)
+    omega, k = p["omega"], p["k"]
+    seeds = W.seeds(24, 6)
+    msg, off = W.messages(W.message_lengths(24, 6, "fixed", 32, 32), 6)
+    pk, sk = orc.keygen_batch(level, seeds)
+    sig, _, _ = orc.sign_batch(level, sk, msg, off)
+    hoff = sig.shape[1] - omega - k
+    kinds = {"unused": 0, "order": 0}
+    for i in range(sig.shape[0]):
+        counts = [int(c) for c in sig[i, hoff + omega:]]
+        variants = []
+        if counts[-1] < omega:
+            t = sig[i].copy()
+            t[hoff + counts[-1]] = 0x5A
+            variants.append(("unused", t))
+        prev = 0
+        for c in counts:
+            if c - prev >= 2:
+                t = sig[i].copy()
+                t[hoff + prev], t[hoff + prev + 1] = t[hoff + prev + 1], t[hoff + prev]
+                variants.append(("order", t))
+                break
+            prev = c
+        m = msg[off[i]:off[i + 1]]
+        o = np.array([0, m.size], dtype=np.uint64)
+        assert orc.verify_batch(level, pk[i:i + 1], m, o, sig[i:i + 1])[0] == 1
+        for kind, t in variants:
+            assert orc.verify_batch(level, pk[i:i + 1], m, o, t[None])[0] == 0, (i, kind)
+            kinds[kind] += 1
+    assert kinds["unused"] > 0 and kinds["order"] > 0
+
+
 def test_empty_message(orc):
     for level in (2, 3, 5):
         pk, sk = orc.keygen(level, bytes(32))
