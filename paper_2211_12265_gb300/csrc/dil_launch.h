@@ -171,6 +171,8 @@ struct ServeCtl {
     int pad1[28];
     int stop;          // set by the host: workers exit once nothing is pending
     int pad2[31];
+    int hhead;         // next ticket for the mu hashers
+    int pad3[31];
 };
 // Per-request record of a Sign (ring slot): the scheduling state shared by
 // the owner and its helpers and the message's mu and rho'.  tref packs the
@@ -229,6 +231,11 @@ struct ServeArgs {
     uint8_t sm_type[SERVE_MAX_SMS]; // home type of each SM (SERVE_TYPE_ANY: serves every type directly)
     int spin_limit;                 // polls of the commit lock
     long long idle_ns;              // an idle worker exits after this long
+    // mu = H(tr || M) precomputed by hasher warps (optional: a worker whose
+    // request has no mu yet hashes the message itself)
+    uint8_t *mu_buf;                // R x 64 bytes
+    unsigned long long *mu_tag;     // R: ticket + 1 of the mu in mu_buf, bit 32 while it is written
+    int hash_sms;                   // SMs 0 .. hash_sms - 1 run only hasher warps
 };
 // Polynomials of one serving worker's scratch (the largest level's keyed
 // Sign or keyed Verify scratch).

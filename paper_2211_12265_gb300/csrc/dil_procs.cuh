@@ -544,16 +544,22 @@ __device__ void sign_prepare(const uint8_t *__restrict__ sk, const uint8_t *__re
 
 // Per-message precomputation of a Sign with a resident key (A^, s^1, s^2, t^0
 // already prepared): mu = H(tr || M) and rho' = H(K || mu) on warp 0.
+// mu_in (nullable, global memory, 8-byte aligned): mu computed beforehand.
 template <int LEVEL, int P>
 __device__ void sign_prepare_keyed(const uint8_t *__restrict__ sk, const uint8_t *__restrict__ msg, size_t mlen,
-                                   GroupSmem &gs, int g, int bar, int lane) {
+                                   GroupSmem &gs, int g, int bar, int lane, const uint8_t *mu_in = nullptr) {
     if (g == 0) {
         gs.hb[HB_K + lane] = __ldg(sk + 32 + lane);
         gs.tr[lane] = __ldg(sk + 64 + lane);
         __syncwarp();
         uint32_t lo = 0, hi = 0;
-        absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
-        squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        if (mu_in) {
+            if (lane < 8)
+                *reinterpret_cast<uint2 *>(gs.hb + HB_MU + 8 * lane) = __ldcg(reinterpret_cast<const uint2 *>(mu_in) + lane);
+        } else {
+            absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
+            squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        }
         __syncwarp();
         lo = 0;
         hi = 0;
@@ -818,11 +824,14 @@ __device__ void sign_zero(uint8_t *sig, int g, int lane) {
 // (KEY_POLYS layout) and `tr` its H(pk), so neither is recomputed.
 // AHAT: `key` is the caller's A^ of this key (k l polynomials, ExpandA(rho));
 // t1 and H(pk) come from pk as in the plain form.
+// mu_in (nullable, KEYED only, global memory, 8-byte aligned): mu computed
+// beforehand.
 template <int LEVEL, int P, bool KEYED = false, bool AHAT = false>
 __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__restrict__ msg, size_t mlen,
                            const uint8_t *__restrict__ sig, int32_t *scratch, GroupSmem &gs, WarpSmem &ws,
                            const int32_t *zt, const int32_t *izt, int g, int bar, int lane,
-                           const int32_t *key = nullptr, const uint8_t *tr = nullptr) {
+                           const int32_t *key = nullptr, const uint8_t *tr = nullptr,
+                           const uint8_t *mu_in = nullptr) {
     using V = Lv<LEVEL>;
     volatile int *vflag = &gs.flag;
     int32_t r[8], acc[8], ch[8];
@@ -895,8 +904,13 @@ __device__ int verify_task(const uint8_t *__restrict__ pk, const uint8_t *__rest
         __syncwarp();
         lo = 0;
         hi = 0;
-        absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
-        squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        if (KEYED && mu_in) {
+            if (lane < 8)
+                *reinterpret_cast<uint2 *>(gs.hb + HB_MU + 8 * lane) = __ldcg(reinterpret_cast<const uint2 *>(mu_in) + lane);
+        } else {
+            absorb_concat(lo, hi, gs.tr, 32, msg, mlen, 136, lane);
+            squeeze_words(lo, hi, gs.hb + HB_MU, 8, lane);
+        }
     }
     group_sync<P>(bar);
     if (*vflag) return 0;

@@ -24,6 +24,10 @@
 // anybody: the only wait is the commit lock, bounded by spin_limit polls
 // (then the request fails with DIL_ETIMEOUT and the error word is set).
 //
+// While requests queue, the warps of a few SMs precompute the requests' mu =
+// H(tr || M) for sixteen messages at a time (the mu hashers below); a worker
+// whose request already has its mu skips that hash.
+//
 // Results go straight to mapped host memory: the signature and status (or
 // the accept byte), a system-scope fence, then the entry (completion number,
 // ticket) in the completion ring that the host polls.  Requests are read
@@ -64,6 +68,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 __device__ __forceinline__ int ld_acquire(const int *p) { return (int)ld_acquire(reinterpret_cast<const unsigned *>(p)); }
 __device__ __forceinline__ unsigned tail_of(const ServeArgs &a) {
     return ld_acquire(reinterpret_cast<const unsigned *>(&a.ctl->tail));
+}
+
+// Tags of precomputed mu (see the mu hashers below).
+constexpr unsigned long long MU_WRITING = 1ull << 32, MU_VALID = 1ull << 33;
+// Warps of the hashing SMs hash while more than HASH_ON published requests
+// wait for a worker, and serve requests again below HASH_OFF.
+constexpr int HASH_ON = 2048, HASH_OFF = 512;
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ long long global_ns() {
@@ -213,12 +229,18 @@ __device__ void own(const ServeArgs &a, unsigned t, const ServeReq &rq, int work
     const ServeKeys &ks = a.keys[LEVEL == 2 ? 0 : LEVEL == 3 ? 1 : 2];
     const bool key_ok = rq.key >= 0 && rq.key < ks.n;
     const uint8_t *msg = a.arena + rq.msg;
+    // a hasher's mu, when the slot's tag names this ticket
+    int have_mu = 0;
+    if (a.hash_sms > 0 && lane == 0) have_mu = ld_acquire64(a.mu_tag + slot) == (MU_VALID | (unsigned long long)(t + 1u));
+    const uint8_t *mu_in = __shfl_sync(FULL, have_mu, 0) ? a.mu_buf + (size_t)slot * 64 : nullptr;
+    __syncwarp();   // the lanes that read mu_in do so after lane 0's acquire
     if (rq.op == 1) {   // Verify
         int r = 0;
         if (key_ok)
             r = verify_task<LEVEL, 1, true>(ks.pk + (size_t)rq.key * V::PK, msg, (size_t)rq.mlen, a.arena + rq.sig,
                                             mine, gs, ws, zt, izt, 0, 0, lane,
-                                            ks.keys + (size_t)rq.key * S::KEY_POLYS * N, ks.tr + (size_t)rq.key * 32);
+                                            ks.keys + (size_t)rq.key * S::KEY_POLYS * N, ks.tr + (size_t)rq.key * 32,
+                                            mu_in);
         if (lane == 0) a.ok[slot] = (uint8_t)r;
         __threadfence_system();
         __syncwarp();
@@ -245,7 +267,7 @@ __device__ void own(const ServeArgs &a, unsigned t, const ServeReq &rq, int work
         tk.fail = 0;
         atomicExch(&tk.tref, ((unsigned long long)t << 32) | 1ull);   // held by the owner
     }
-    sign_prepare_keyed<LEVEL, 1>(ks.sk + (size_t)rq.key * V::SK, msg, (size_t)rq.mlen, gs, 0, 0, lane);
+    sign_prepare_keyed<LEVEL, 1>(ks.sk + (size_t)rq.key * V::SK, msg, (size_t)rq.mlen, gs, 0, 0, lane, mu_in);
     tk.mu[lane] = gs.hb[HB_MU + lane];
     tk.mu[32 + lane] = gs.hb[HB_MU + 32 + lane];
     tk.rhop[lane] = gs.rhop[lane];
@@ -372,6 +394,150 @@ __device__ unsigned find_and_join(const ServeArgs &a, int nworkers, unsigned spe
     return joined ? found : NO_TICKET;
 }
 
+// ------------------------------------------------------------- mu hashers
+// mu = H(tr || M) of published requests, precomputed in the sixteen-state
+// form (about a sixth of the 25-lane form's cost per block under load) by the
+// warps of the first hash_sms SMs while more than HASH_ON published requests
+// wait for a worker (below HASH_OFF they serve requests like any worker; on
+// SMs of their own they add no code to the SMs that serve one request type).
+// Each of a hasher's sixteen instances absorbs one request's tr || M block by
+// block and, once its message is done, writes mu to the request's slot and
+// takes the next ticket, so instances never wait for one another's messages.  A worker uses a request's mu only when the slot's tag
+// names that request's ticket; otherwise it hashes the message itself, so no
+// worker ever waits for a hasher and a hasher may fall behind, skip or
+// abandon tickets.  Tag protocol (64-bit word per slot): MU_VALID | (t + 1)
+// once ticket t's mu is in the slot; a hasher claims the slot with
+// MU_WRITING | (t + 1) by compare-and-swap only from a finished tag of an
+// older ticket, so a stale hash never lands over a newer one.  A newer ticket
+// of the same slot is published only after ticket t completed, so the mu a
+// worker reads cannot change under it.
+// Lane `lane` (< 17)'s 8 bytes of 136-byte block blk of tr (32 bytes, 8-byte
+// aligned) || msg (mlen bytes, 8-byte aligned in the arena), padded in the
+// final block.  The message is read in aligned words through L2 (the host
+// writes the arena while the kernel runs); bytes past its end are masked.
+__device__ __forceinline__ uint64_t mu_block_word(const uint8_t *tr, const uint8_t *msg, size_t mlen, int blk,
+                                                  int total, int lane) {
+    const size_t off = (size_t)blk * 136 + 8 * lane;
+    uint64_t w = 0;
+    if (off < 32) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(tr + off));
+        w = ((uint64_t)v.y << 32) | v.x;
+    } else if (off - 32 < mlen) {
+        w = ld_word_cg(msg + (off - 32));
+        const size_t have = mlen - (off - 32);
+        if (have < 8) w &= (1ull << (8 * have)) - 1;
+    }
+    if (blk == total - 1) pad_word(w, (int)(32 + mlen - (size_t)blk * 136), 136, lane);
+    return w;
+}
+
+// Writes instance s's mu (stream words 0..15) for ticket t if the slot takes it.
+__device__ void publish_mu(const ServeArgs &a, unsigned t, const uint32_t *kst, int s, int lane) {
+    const unsigned slot = t & (unsigned)(a.ring - 1);
+    unsigned long long *tag = a.mu_tag + slot;
+    int won = 0;
+    if (lane == 0) {
+        const unsigned long long cur = atomicAdd(tag, 0ull);
+        won = !(cur & MU_WRITING) && (int)((t + 1u) - (unsigned)cur) > 0 &&
+              atomicCAS(tag, cur, MU_WRITING | (unsigned long long)(t + 1u)) == cur;
+    }
+    if (!__shfl_sync(FULL, won, 0)) return;
+    if (lane < 16) reinterpret_cast<uint32_t *>(a.mu_buf + (size_t)slot * 64)[lane] = kst[k16_word(s, lane)];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(tag, MU_VALID | (unsigned long long)(t + 1u));
+}
+
+// Published requests not yet taken by a worker (head may run ahead of tail:
+// idle workers hold the next numbers).
+__device__ __forceinline__ int backlog(const ServeArgs &a) {
+    return (int)(tail_of(a) - (unsigned)ld_acquire(&a.ctl->head));
+}
+
+// One hasher pass loop of a warp on a hashing SM; lane s < 16 keeps instance
+// s's request.  Returns true when the host set stop, false once the backlog
+// falls below HASH_OFF (the warp then serves requests like any worker; the
+// hashes it leaves unfinished are simply not used).
+__device__ bool hash_worker(const ServeArgs &a, uint32_t *kst, int lane) {
+    unsigned t = 0;
+    int state = 0;   // 0 free, 1 holding an unpublished ticket, 2 absorbing
+    const uint8_t *msg = nullptr, *tr = nullptr;
+    size_t mlen = 0;
+    int total = 0, next = 0;
+    for (;;) {
+        // lane 0 reads the control words once per pass (the serving workers poll the same line)
+        int stop = 0, low = 0;
+        unsigned tail = 0, head = 0;
+        if (lane == 0) {
+            stop = ld_acquire(&a.ctl->stop);
+            tail = tail_of(a);
+            head = (unsigned)ld_acquire(&a.ctl->head);
+            low = (int)(tail - head) < HASH_OFF;
+            // tickets the workers have taken are not worth hashing: move the hashers' counter up
+            const unsigned hh = *reinterpret_cast<volatile unsigned *>(&a.ctl->hhead);
+            if ((int)(head - hh) > 0) atomicCAS(reinterpret_cast<unsigned *>(&a.ctl->hhead), hh, head);
+        }
+        if (__shfl_sync(FULL, stop, 0)) return true;
+        if (__shfl_sync(FULL, low, 0)) return false;
+        tail = __shfl_sync(FULL, tail, 0);
+        __syncwarp();   // descriptor loads below come after lane 0's acquire of tail
+        if (lane < 16) {
+            if (state == 0) {
+                t = atomicAdd(reinterpret_cast<unsigned *>(&a.ctl->hhead), 1u);
+                state = 1;
+            }
+            if (state == 1 && (int)(tail - t) > 0) {
+                const ServeReq rq = load_req(a, t);
+                const ServeKeys &ks = a.keys[rq.level == 2 ? 0 : rq.level == 3 ? 1 : 2];
+                state = 0;
+                if (rq.key >= 0 && rq.key < ks.n) {   // unknown keys are answered without a mu
+                    tr = ks.tr + (size_t)rq.key * 32;
+                    msg = a.arena + rq.msg;
+                    mlen = (size_t)rq.mlen;
+                    total = (int)((32 + mlen) / 136) + 1;
+                    next = 0;
+                    state = 2;
+                }
+            }
+        }
+        const unsigned active = __ballot_sync(FULL, lane < 16 && state == 2);
+        if (!active) {
+            __nanosleep(500);
+            continue;
+        }
+        // absorb each active instance's next block (lanes 0..24 cover its 25 state lanes)
+        for (unsigned m = active; m; m &= m - 1) {
+            const int s = __ffs(m) - 1;
+            const uint8_t *ms = reinterpret_cast<const uint8_t *>(
+                __shfl_sync(FULL, reinterpret_cast<unsigned long long>(msg), s));
+            const uint8_t *ts = reinterpret_cast<const uint8_t *>(
+                __shfl_sync(FULL, reinterpret_cast<unsigned long long>(tr), s));
+            const size_t ml = (size_t)__shfl_sync(FULL, (unsigned long long)mlen, s);
+            const int tot = __shfl_sync(FULL, total, s), blk = __shfl_sync(FULL, next, s);
+            if (lane < 25) {
+                const uint64_t w = lane < 17 ? mu_block_word(ts, ms, ml, blk, tot, lane) : 0;
+                uint32_t *st = kst + k16_slot(lane, 2 * s);
+                if (blk == 0) {
+                    st[0] = (uint32_t)w;
+                    st[1] = (uint32_t)(w >> 32);
+                } else {
+                    st[0] ^= (uint32_t)w;
+                    st[1] ^= (uint32_t)(w >> 32);
+                }
+            }
+        }
+        __syncwarp();
+        keccak16_permute(kst);
+        if (lane < 16 && state == 2) ++next;
+        const unsigned done = __ballot_sync(FULL, lane < 16 && state == 2 && next == total);
+        for (unsigned m = done; m; m &= m - 1) {
+            const int s = __ffs(m) - 1;
+            publish_mu(a, __shfl_sync(FULL, t, s), kst, s, lane);
+        }
+        if (lane < 16 && state == 2 && next == total) state = 0;
+    }
+}
+
 __device__ __forceinline__ unsigned sm_id() {
     unsigned id;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
@@ -403,11 +569,20 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32, 4) k_serve(ServeArgs a) {
     uint8_t *stage = a.sig_stage + (size_t)worker * SERVE_SIG_STRIDE;
     unsigned cursor = (unsigned)worker * 2654435761u % (unsigned)nworkers;
     const unsigned smid = sm_id();
+    const bool hashing_sm = (int)smid < a.hash_sms;   // its warps hash mu while requests queue
     const int home = smid < SERVE_MAX_SMS ? a.sm_type[smid] : SERVE_TYPE_ANY;
     unsigned ticket = 0;
     bool holding = false;
     long long waiting_since = -1;
     for (;;) {
+        if (!holding && hashing_sm) {
+            int busy = 0;
+            if (lane == 0) busy = backlog(a) > HASH_ON;
+            if (__shfl_sync(FULL, busy, 0)) {
+                if (hash_worker(a, ws.k16, lane)) break;   // stop: nothing of this warp is in flight
+                continue;
+            }
+        }
         if (!holding) {
             if (home != SERVE_TYPE_ANY) {   // tickets of the home type forwarded from other SMs first
                 unsigned f = 0;

@@ -181,6 +181,8 @@ struct Ring {
     uint8_t *d_sig_stage = nullptr;     // per worker: a signature packed before it goes to mapped memory
     dil::ServeFifo *d_fifo = nullptr;   // forwarding queues by request type
     unsigned long long *d_fifo_ring = nullptr;
+    uint8_t *d_mu = nullptr;                 // R x 64: mu precomputed by the hasher warps
+    unsigned long long *d_mu_tag = nullptr;  // R: which ticket's mu a slot holds
     unsigned long long *h_fifo_init = nullptr;   // pinned: the queues' entries as every launch starts them
     int sms = 0;
     double type_work[dil::SERVE_TYPES] = {};    // recent warp time per request type (publisher), for the SM shares
@@ -230,6 +232,11 @@ constexpr int RING_FIFO_PER_SM = 16;          // forwarding stops while a queue 
 // repetitions take issue slots from the requests on its SM.  On the serving
 // mix: p99 1.8 ms at half load against 5.7 ms with helpers up to 80% busy,
 // and 4.3 M ops/s saturated against 4.07 M without helpers.
+// SMs whose warps hash mu = H(tr || M) while requests queue (the serving
+// kernel's mu hashers): on the serving mix, 4.33-4.38 M ops/s saturated
+// without them, 4.55-4.65 M with 6-12 such SMs, p99 unchanged at quarter and
+// half load and 3-6% lower at 75% load.
+constexpr int RING_HASH_SMS = 12;
 constexpr int SERVE_SPEC = 4;
 constexpr int SERVE_HELP_BELOW_PCT = 10;
 // Warp time of one request by type in microseconds (GB300, 32 of 32 warps per
@@ -492,6 +499,7 @@ void ring_free(Ring &g) {
     cudaFree(g.d_ctl); cudaFree(g.d_req); cudaFree(g.d_arena); cudaFree(g.d_tasks);
     cudaFree(g.d_worker_ticket); cudaFree(g.d_scratch); cudaFree(g.d_sig_stage);
     cudaFree(g.d_fifo); cudaFree(g.d_fifo_ring); cudaFreeHost(g.h_fifo_init);
+    cudaFree(g.d_mu); cudaFree(g.d_mu_tag);
     cudaFreeHost(g.h_req); cudaFreeHost(g.h_arena); cudaFreeHost(g.h_words);
     cudaFreeHost(g.m_sig); cudaFreeHost(g.m_status); cudaFreeHost(g.m_iters); cudaFreeHost(g.m_ok);
     cudaFreeHost(g.m_comp);
@@ -546,6 +554,8 @@ bool ring_alloc(Ring &g, int device, size_t budget, size_t msg_cap) {
               cudaMalloc(&g.d_sig_stage, (size_t)g.workers * dil::SERVE_SIG_STRIDE) == cudaSuccess &&
               cudaMalloc(&g.d_fifo, dil::SERVE_TYPES * sizeof(dil::ServeFifo)) == cudaSuccess &&
               cudaMalloc(&g.d_fifo_ring, dil::SERVE_TYPES * R * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&g.d_mu, R * 64) == cudaSuccess &&
+              cudaMalloc(&g.d_mu_tag, R * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&g.h_fifo_init, dil::SERVE_TYPES * R * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&g.h_req, R * sizeof(dil::ServeReq)) == cudaSuccess &&
               cudaMallocHost(&g.h_arena, arena) == cudaSuccess &&
@@ -558,7 +568,8 @@ bool ring_alloc(Ring &g, int device, size_t budget, size_t msg_cap) {
     if (ok) {
         ok = cudaMemset(g.d_ctl, 0, sizeof(dil::ServeCtl)) == cudaSuccess &&
              cudaMemset(g.d_worker_ticket, 0xFF, (size_t)g.workers * sizeof(int)) == cudaSuccess &&
-             cudaMemset(g.d_tasks, 0, R * sizeof(dil::ServeTask)) == cudaSuccess;
+             cudaMemset(g.d_tasks, 0, R * sizeof(dil::ServeTask)) == cudaSuccess &&
+             cudaMemset(g.d_mu_tag, 0, R * sizeof(unsigned long long)) == cudaSuccess;
         // completion entry i first expects completion number i: start every
         // entry at a number it cannot hold then
         for (size_t i = 0; ok && i < R; ++i) g.m_comp[i] = (unsigned long long)(unsigned)(i - R) << 32;
@@ -611,7 +622,8 @@ void assign_home_types(Ring &g, dil::ServeArgs &a) {
     for (int ty = 0; ty < dil::SERVE_TYPES; ++ty) a.type_sms[ty] = 0;
     double total = 0;
     for (double w : g.type_work) total += w;
-    const int sms = std::min(g.sms, dil::SERVE_MAX_SMS);
+    const int first = a.hash_sms;   // SMs before it only hash
+    const int sms = std::min(g.sms, dil::SERVE_MAX_SMS) - first;
     int active_types = 0;
     for (double w : g.type_work) active_types += w > 0;
     if (total <= 0 || sms < active_types) return;
@@ -638,7 +650,7 @@ void assign_home_types(Ring &g, dil::ServeArgs &a) {
         a.type_sms[big]--;
         --given;
     }
-    int s = 0;
+    int s = first;
     for (int ty = 0; ty < dil::SERVE_TYPES; ++ty)
         for (int k = 0; k < a.type_sms[ty]; ++k) a.sm_type[s++] = (uint8_t)ty;
     for (double &w : g.type_work) w *= 0.5;
@@ -659,7 +671,8 @@ bool ring_launch(dil_server *sv) {
             std::this_thread::yield();
         }
     }
-    if (!ring_copy_word(g, reinterpret_cast<unsigned *>(&g.d_ctl->head), g.oldest.load(std::memory_order_acquire)))
+    if (!ring_copy_word(g, reinterpret_cast<unsigned *>(&g.d_ctl->head), g.oldest.load(std::memory_order_acquire)) ||
+        !ring_copy_word(g, reinterpret_cast<unsigned *>(&g.d_ctl->hhead), g.oldest.load(std::memory_order_acquire)))
         return false;
     if (g.stop_set) {
         if (!ring_copy_word(g, reinterpret_cast<unsigned *>(&g.d_ctl->stop), 0)) return false;
@@ -696,9 +709,16 @@ bool ring_launch(dil_server *sv) {
     a.fifo = g.d_fifo;
     a.fifo_ring = g.d_fifo_ring;
     a.fifo_limit = RING_FIFO_PER_SM;
+    // hashing SMs only when at least one CTA per SM lands elsewhere (an SM
+    // holds at most 8 CTAs of 8 warps): their warps hash only while requests
+    // queue, and the requests must still be served by other SMs' workers
+    a.hash_sms = std::min(RING_HASH_SMS, g.sms / 4);
+    if (g.grid < a.hash_sms * 8 + g.sms) a.hash_sms = 0;
     assign_home_types(g, a);
     a.spin_limit = dil::PERSIST_SPIN_LIMIT;
     a.idle_ns = 10000000000ll;   // a ticket unpublished for 10 s (the host stops an idle kernel long before)
+    a.mu_buf = g.d_mu;
+    a.mu_tag = g.d_mu_tag;
     ok = ok && cudaEventRecord(g.ev_pub, g.cstream) == cudaSuccess &&
          cudaStreamWaitEvent(g.kstream, g.ev_pub, 0) == cudaSuccess &&
          dil::launch_serve(a, g.grid, g.kstream) == cudaSuccess &&
