@@ -331,6 +331,11 @@ int dil_server_replay(dil_server *srv, size_t n, const double *arrival_s, const 
  * carried and kernel launches (keyed-kernel launches of static batches,
  * serving-kernel launches) since creation.  Any output pointer may be NULL. */
 int dil_server_stats(const dil_server *srv, uint64_t *batches, uint64_t *requests, uint64_t *launches);
+/* Test-only: the number of requests the serving kernel served with a mu =
+ * H(tr || M) precomputed by its hasher warps (they hash while more than 2048
+ * published requests wait for a worker), since the server was created.
+ * Synchronous read of a device counter; DIL_EINVAL for NULL arguments. */
+int dil_test_server_mu_hashed(const dil_server *srv, uint64_t *count);
 
 /* Host-buffer forms of the three operations (all pointers are HOST pointers;
  * msg_off too; pinned memory lets the copies overlap).  They copy inputs to

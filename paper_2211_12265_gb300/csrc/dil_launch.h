@@ -173,6 +173,8 @@ struct ServeCtl {
     int pad2[31];
     int hhead;         // next ticket for the mu hashers
     int pad3[31];
+    int mu_used;       // requests served with a hasher's mu (a test reads it)
+    int pad4[31];
 };
 // Per-request record of a Sign (ring slot): the scheduling state shared by
 // the owner and its helpers and the message's mu and rho'.  tref packs the

@@ -234,6 +234,7 @@ __device__ void own(const ServeArgs &a, unsigned t, const ServeReq &rq, int work
     if (a.hash_sms > 0 && lane == 0) have_mu = ld_acquire64(a.mu_tag + slot) == (MU_VALID | (unsigned long long)(t + 1u));
     const uint8_t *mu_in = __shfl_sync(FULL, have_mu, 0) ? a.mu_buf + (size_t)slot * 64 : nullptr;
     __syncwarp();   // the lanes that read mu_in do so after lane 0's acquire
+    if (mu_in && lane == 0) atomicAdd(&a.ctl->mu_used, 1);
     if (rq.op == 1) {   // Verify
         int r = 0;
         if (key_ok)

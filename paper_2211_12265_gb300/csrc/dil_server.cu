@@ -1296,4 +1296,18 @@ int dil_server_stats(const dil_server *sv, uint64_t *batches, uint64_t *requests
     return DIL_OK;
 }
 
+int dil_test_server_mu_hashed(const dil_server *sv, uint64_t *count) {
+    if (!sv || !count) return DIL_EINVAL;
+    *count = 0;
+    if (!sv->ring.d_ctl) return DIL_OK;
+    int v = 0;
+    cudaSetDevice(sv->device);
+    if (cudaMemcpy(&v, &sv->ring.d_ctl->mu_used, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return DIL_ECUDA;
+    }
+    *count = (uint64_t)(unsigned)v;
+    return DIL_OK;
+}
+
 }  // extern "C"

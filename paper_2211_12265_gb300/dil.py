@@ -99,6 +99,7 @@ def load() -> ctypes.CDLL:
                 "dil_server_cancel": [P, ctypes.c_uint64],
                 "dil_server_replay": [P, S, P, P, P, P, P, P, P, P, P, P, P, P],
                 "dil_server_stats": [P, P, P, P],
+                "dil_test_server_mu_hashed": [P, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -455,6 +456,13 @@ def dil_server_stats(srv) -> tuple[int, int, int]:
     b, r, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(load().dil_server_stats(srv, ctypes.byref(b), ctypes.byref(r), ctypes.byref(k)), "dil_server_stats")
     return b.value, r.value, k.value
+
+
+def dil_test_server_mu_hashed(srv) -> int:
+    """Requests served with a precomputed mu since the server was created."""
+    c = ctypes.c_uint64()
+    _check(load().dil_test_server_mu_hashed(srv, ctypes.byref(c)), "dil_test_server_mu_hashed")
+    return c.value
 
 
 # ----------------------------------------------------------------- wrapper

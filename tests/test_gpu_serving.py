@@ -344,3 +344,19 @@ def test_server_edge_lengths_and_unknown_keys(keys, orc, policy):
         assert np.array_equal(out["sig"][i, :sigb], exp_sig[i, :sigb]), f"request {i} (len {lens[i]})"
     assert np.array_equal(out["ok"][~sign], exp_ok[~sign])
     assert bad[sign].any() and bad[~sign].any()
+
+
+def test_server_burst_with_precomputed_mu(keys, orc):
+    """A burst of 40,000 requests (enough that requests queue for several
+    milliseconds and the hasher warps precompute mu = H(tr || M)): every
+    result equals the oracle's, with rejections, at all levels, and some
+    requests were served with a precomputed mu."""
+    from paper_2211_12265_gb300 import dil, serving
+    req, exp = oracle_trace(orc, keys, 40000, 1e9, seed=306, hi=1024)
+    with serving.Server(0, memory_budget=2 << 30, streams=2, max_batch=4096) as srv:
+        for lv in keys:
+            srv.add_keys(lv, *keys[lv])
+        out = srv.replay(req)
+        hashed = dil.dil_test_server_mu_hashed(srv.handle)
+    assert_matches_oracle(req, out, exp)
+    assert hashed > 0, "no request was served with a precomputed mu"
