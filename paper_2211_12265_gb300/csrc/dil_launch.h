@@ -106,6 +106,10 @@ struct PersistJobs {
     PersistJob job[PERSIST_MAX_JOBS];
     int njobs;
     int total;
+    // home job of each SM: SMs [sm_end[j - 1], sm_end[j]) take job j's fresh
+    // tasks first (one level's task body per SM while the jobs last), then
+    // the other jobs'; the host splits the SMs in proportion to each job's work
+    int sm_end[PERSIST_MAX_JOBS];
 };
 // Per-task scheduling record (device memory, initialised by the task's owner).
 struct PersistTask {
@@ -119,10 +123,11 @@ struct PersistTask {
 };
 // Queue header (device memory, zeroed before each launch).
 struct PersistQueue {
-    int next_task;
+    int next_task;    // unused since the per-job cursors
     int error;        // DIL_ETIMEOUT when a bounded wait ran out
     int cancel;       // set by the host (dil_persistent_cancel) while the launch runs
-    int pad[29];
+    int next_job[PERSIST_MAX_JOBS];   // per job: next fresh task (job-local index)
+    int pad[26];
 };
 struct PersistTuning {
     int warps = 8;        // warps per CTA

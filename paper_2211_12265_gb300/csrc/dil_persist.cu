@@ -278,26 +278,44 @@ __global__ void __launch_bounds__(256, 4) k_sign_persist(PersistJobs J, PersistQ
     bool canceled = false, fresh = true;
     int cur = 0, end = 0;
     int start = (int)(((unsigned)slot * 2654435761u) % (unsigned)pc.slots);
+    // the job whose fresh tasks this SM takes first (leader only); advances
+    // once that job's tasks are all claimed
+    int home = 0;
+    if (leader) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        while (home + 1 < J.njobs && (int)smid >= J.sm_end[home]) ++home;
+    }
     for (int round = 0; round < 4096;) {
         int t, s;
         bool own;
         if (fresh) {
             if (cur >= end) {
-                if (leader) {
-                    gs.claim = atomicAdd(&q->next_task, chunk);
+                if (leader) {   // up to `chunk` fresh tasks of the home job, else of the next job with any left
+                    int got = -1;
+                    for (int k = 0; k < J.njobs && got < 0; ++k) {
+                        const int c = atomicAdd(&q->next_job[home], chunk);
+                        if (c < J.job[home].n)
+                            got = J.job[home].start + c;
+                        else
+                            home = (home + 1) % J.njobs;
+                    }
+                    gs.claim = got;
                     gs.claim2 = ld_l2(&q->cancel);
                 }
                 group_sync<P>(bar);
                 const int c0 = *(volatile int *)&gs.claim;
                 canceled = *(volatile int *)&gs.claim2 != 0;
                 group_sync<P>(bar);
-                if (c0 >= J.total) {
+                if (c0 < 0) {
                     fresh = false;
                     if (spec <= 0 || canceled || ld_l2(&q->cancel)) break;
                     continue;
                 }
+                int local;
+                const PersistJob &jc = job_of(J, c0, local);
                 cur = c0;
-                end = min(c0 + chunk, J.total);
+                end = jc.start + min(local + chunk, jc.n);
             }
             t = cur++;
             s = slot;
